@@ -1,0 +1,242 @@
+/*
+ * mpwsd.h -- C ABI of libmpwsd, a GB300 (sm_103a) implementation of two-stage
+ * near-ML decoding with multipoint code-weight sphere decoding (MP-WSD),
+ * arXiv 2602.08501.
+ *
+ * The decoder has two stages (Sec. III):
+ *   stage 1  CRC-aided SC-list decoding of every frame; the most reliable
+ *            candidate is checked by the CRC and, if it passes, is the output
+ *            (Sec. III-A);
+ *   stage 2  for the frames that fail, every list entry is an anchor; each
+ *            (frame, anchor) trajectory repeatedly moves to the best codeword
+ *            of its code-weight sphere S_r(c) = c xor S_r(0) (Eqs. (2)-(4)),
+ *            found by scoring every precomputed low-weight pattern p with the
+ *            correlation gain of Eq. (5), and stops when nothing strictly
+ *            improves or after T iterations; the frame's output is the
+ *            trajectory end point of smallest Euclidean distance
+ *            (Algorithm 1).
+ *
+ * Conventions used by every entry point:
+ *   - n = 2^m with n in {32, 64, 128}; W = (n + 63) / 64 words per bit vector.
+ *   - Bit vectors (codewords, patterns) are packed little-endian: bit j of
+ *     word j / 64 is position j.
+ *   - The code is the Arikan form c = u [[1,0],[1,1]]^{(x)m} restricted to
+ *     the non-frozen rows (Reed-Muller codes are the frozen sets that keep
+ *     rows of weight >= 2^(m-r)).
+ *   - Received samples y are FP32. Stage 1 and every exact comparison work on
+ *     the integer image round(y * 2^19) clamped to +-(2^23 - 1); inputs that
+ *     are already multiples of 2^-19 with |y| < 16 are used exactly.
+ *   - "device" pointers are CUDA device memory of the device that was current
+ *     when the code handle was created; "host" pointers are ordinary memory.
+ *     The caller owns every buffer it passes; the library never keeps a
+ *     caller pointer after the call returns (asynchronous work on a stream
+ *     reads/writes the caller's device buffers until the stream reaches it).
+ *   - Every function returns an int status (0 = MPWSD_OK, < 0 = error) and
+ *     never aborts or exits. mpwsd_last_error() gives a message for the
+ *     calling thread's most recent failure.
+ */
+#ifndef MPWSD_H
+#define MPWSD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MPWSD_API __attribute__((visibility("default")))
+#else
+#define MPWSD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define MPWSD_OK 0
+#define MPWSD_EINVAL (-1)       /* an argument is out of range or inconsistent */
+#define MPWSD_ENOMEM (-2)       /* a device or host allocation failed; handles stay usable */
+#define MPWSD_ECUDA (-3)        /* a CUDA runtime call or kernel launch failed */
+#define MPWSD_ETIMEOUT (-4)     /* a bounded device-side wait gave up (see mpwsd_sync) */
+#define MPWSD_EUNSUPPORTED (-5) /* valid request this build does not implement */
+
+/* ---- limits ------------------------------------------------------------- */
+#define MPWSD_MAX_L 32          /* list size / anchors per frame */
+#define MPWSD_MAX_T 15          /* stage-2 iterations (J of Algorithm 1) */
+#define MPWSD_TOPK 4            /* candidates kept per trajectory by the scoring kernels */
+
+/* ---- options ------------------------------------------------------------ */
+#define MPWSD_SCORE_BF16X2 0    /* tcgen05 tensor cores, y split into bf16 hi + lo, FP32 accumulate */
+#define MPWSD_SCORE_FP32 1      /* FP32 CUDA cores, sparse gather-add over each pattern's support */
+
+#define MPWSD_RULE_TOP1 0       /* stage 1 succeeds iff the best-metric list entry passes the CRC (Sec. III-A) */
+#define MPWSD_RULE_ANY 1        /* stage 1 succeeds with the best-metric entry that passes the CRC */
+
+/* Output flag bits (one uint16 per frame). */
+#define MPWSD_FLAG_STAGE2 0x0001u   /* stage 2 ran for this frame */
+#define MPWSD_FLAG_CRC_OK 0x0002u   /* the output codeword passes the CRC */
+#define MPWSD_FLAG_RESCAN 0x0004u   /* some trajectory needed a full FP64 rescan (near-tie overflow) */
+#define MPWSD_FLAG_ITERS_SHIFT 4    /* bits 4..7: stage-2 iterations used (0 if stage 2 did not run) */
+#define MPWSD_FLAG_ERROR 0x0100u    /* a device-side wait timed out; the frame's output is not valid */
+
+typedef struct mpwsd_opts {
+    int score_mode;  /* MPWSD_SCORE_BF16X2 (default) or MPWSD_SCORE_FP32 */
+    int stage1_rule; /* MPWSD_RULE_TOP1 (default) or MPWSD_RULE_ANY */
+    int always_on;   /* nonzero: run stage 2 on every frame, CRC or not (always-on mode, Sec. III-C) */
+    int reserved[5]; /* must be zero */
+} mpwsd_opts;
+
+/* Counters accumulated on the device by every decode of a code handle since
+ * the last mpwsd_stats_reset. */
+typedef struct mpwsd_stats {
+    int64_t frames;            /* frames decoded */
+    int64_t stage2_frames;     /* frames that ran stage 2 (P_act = stage2_frames / frames, Eq. (7)) */
+    int64_t trajectories;      /* (frame, anchor) trajectories started */
+    int64_t pattern_evals;     /* (active trajectory, pattern) pairs scored, over all iterations */
+    int64_t rerank_candidates; /* candidates re-scored exactly in FP64 */
+    int64_t rescans;           /* trajectories that needed a full FP64 rescan */
+    int64_t hops;              /* strict-improvement moves taken */
+    int64_t kernel_launches;   /* kernels launched by the library (host-side count) */
+} mpwsd_stats;
+
+typedef struct mpwsd_code mpwsd_code;           /* opaque, owned by the library */
+typedef struct mpwsd_workspace mpwsd_workspace; /* opaque, owned by the library */
+
+/* Human-readable name of a status code (static storage). */
+MPWSD_API const char *mpwsd_strerror(int status);
+
+/* Message describing the calling thread's most recent failed call ("" if none). */
+MPWSD_API const char *mpwsd_last_error(void);
+
+/*
+ * mpwsd_load_code -- validate a code and its move-pattern set and upload them.
+ * Code model: Sec. II-B (c = mG, CRC precoding v = [m, crc(m)]); pattern set:
+ * the code-weight sphere S_r(0) without 0, Sec. II-C Eqs. (1)-(3).
+ *
+ *   n           code length, 32, 64 or 128.
+ *   G           host, k x n bytes (0/1), or NULL. If given it must equal the
+ *               rows of [[1,0],[1,1]]^{(x)m} at the non-frozen indices in
+ *               ascending order; the library uses only the frozen set.
+ *   frozen      host, n bytes, 1 = frozen (u_i = 0), 0 = information.
+ *   k_info      message bits; k = #non-frozen = k_info + crc_len.
+ *   crc_poly    CRC generator without its leading term: g(x) = x^crc_len +
+ *               sum_b bit_b(crc_poly) x^b (x^6 + x^5 + 1 -> 0x21). The CRC is
+ *               the remainder of m(x) x^crc_len mod g(x), message bit 0 the
+ *               highest power, zero initial value, no reflection, no final XOR;
+ *               v = [m_0..m_{k_info-1}, r_0..r_{crc_len-1}] fills the
+ *               information indices in ascending order.
+ *   crc_len     0..32; 0 = no CRC (stage 2 then runs on every frame).
+ *   patterns    host, n_patterns x W words: nonzero, distinct codewords. Their
+ *               order is the tie-break order of stage 2 (lower index wins).
+ *   n_patterns  1 .. 2^31 - 1.
+ *   out         receives the handle.
+ *
+ * Returns MPWSD_EINVAL if G does not match the frozen set, if a pattern is 0,
+ * not a codeword, or repeated, or if k_info + crc_len != k; MPWSD_ENOMEM if
+ * device memory runs out; MPWSD_ECUDA on a CUDA failure. The inputs are
+ * copied; the caller may free them when the call returns. Synchronous.
+ */
+MPWSD_API int mpwsd_load_code(int n, const uint8_t *G, const uint8_t *frozen, int k_info, uint32_t crc_poly, int crc_len,
+                    const uint64_t *patterns, int64_t n_patterns, mpwsd_code **out);
+
+/* Release a code handle and everything it owns (waits for the device). NULL is a no-op. */
+MPWSD_API void mpwsd_free_code(mpwsd_code *code);
+
+/* Code parameters as loaded: any pointer may be NULL. */
+MPWSD_API int mpwsd_code_info(const mpwsd_code *code, int *n, int *k, int64_t *n_patterns, int *max_pattern_weight);
+
+/*
+ * mpwsd_decode -- two-stage decode of B frames (Sec. III, Algorithm 1).
+ *
+ *   y_dev     device, B x n FP32, row-major (frame f at y_dev + f*n).
+ *   B         frames, >= 0 (0 launches nothing).
+ *   L         list size of stage 1 = anchors of stage 2, 1..MPWSD_MAX_L.
+ *   T         stage-2 iterations J, 1..MPWSD_MAX_T.
+ *   opts      NULL for defaults (BF16X2 scoring, TOP1 rule, CRC gating).
+ *   cw_dev    device, B x W uint64: decoded codewords (written asynchronously).
+ *   flags_dev device, B uint16: MPWSD_FLAG_* bits per frame.
+ *   stream    cudaStream_t (NULL = legacy default stream); all work is
+ *             enqueued on it and the call returns without waiting.
+ *
+ * Arguments are checked before anything is enqueued (MPWSD_EINVAL). Uses the
+ * handle's internal workspace, grown on demand with cudaMalloc (a growth
+ * waits for the device); concurrent calls on one handle must be serialised
+ * by the caller -- use mpwsd_decode_ws with one workspace per caller instead.
+ * A device-side timeout is reported by MPWSD_FLAG_ERROR on the affected
+ * frames and by the next mpwsd_sync.
+ */
+MPWSD_API int mpwsd_decode(mpwsd_code *code, const float *y_dev, int64_t B, int L, int T, const mpwsd_opts *opts,
+                 uint64_t *cw_dev, uint16_t *flags_dev, void *stream);
+
+/*
+ * mpwsd_workspace_create -- device scratch for decodes of up to max_B frames
+ * with lists of up to max_L. One workspace may be used by one stream at a
+ * time; several workspaces let several streams decode concurrently with one
+ * code handle (continuous batching). MPWSD_ENOMEM when device memory is
+ * short (the admission-refusal signal of a serving loop).
+ */
+MPWSD_API int mpwsd_workspace_create(const mpwsd_code *code, int64_t max_B, int max_L, mpwsd_workspace **out);
+
+/* Release a workspace (waits for the device). NULL is a no-op. */
+MPWSD_API void mpwsd_workspace_free(mpwsd_workspace *ws);
+
+/* Bytes of device memory a workspace for (max_B, max_L) takes (no allocation). */
+MPWSD_API int mpwsd_workspace_bytes(const mpwsd_code *code, int64_t max_B, int max_L, size_t *bytes);
+
+/* mpwsd_decode with a caller-provided workspace (B <= its max_B, L <= its max_L). */
+MPWSD_API int mpwsd_decode_ws(mpwsd_code *code, mpwsd_workspace *ws, const float *y_dev, int64_t B, int L, int T,
+                    const mpwsd_opts *opts, uint64_t *cw_dev, uint16_t *flags_dev, void *stream);
+
+/*
+ * mpwsd_stage1_list -- stage 1 alone (Sec. III-A): min-sum SC-list decoding
+ * of B frames, returning the whole final list in order (best metric first).
+ *
+ *   list_cw_dev  device, B x L x W uint64: candidate codewords.
+ *   list_pm_dev  device, B x L int64: path metrics in units of 2^-19.
+ * Entries past the list size min(L, 2^k) are not written. Asynchronous.
+ */
+MPWSD_API int mpwsd_stage1_list(mpwsd_code *code, const float *y_dev, int64_t B, int L, uint64_t *list_cw_dev,
+                      int64_t *list_pm_dev, void *stream);
+
+/*
+ * mpwsd_score_topk -- the scoring step of stage 2 alone: for each row r,
+ * the trajectory centre c_r (frame frame_dev[r] of y_dev) gets the scores
+ * S(r, p) = sum_{j in supp p} y_j x_j(c_r) for every pattern p (-G/2 of
+ * Eq. (5); ED(c xor p) - ED(c) = 4 S), and the MPWSD_TOPK smallest are
+ * returned in ascending order (equal scores in ascending pattern index).
+ * Scores are the kernel's approximations (mode BF16X2 or FP32), not exact.
+ *
+ *   y_dev       device, B x n FP32.       frame_dev  device, M int32 in [0, B).
+ *   cw_dev      device, M x W uint64.     M          rows, >= 0.
+ *   topk_val_dev device, M x MPWSD_TOPK FP32; topk_idx_dev device, M x
+ *   MPWSD_TOPK int32 (-1 where fewer than MPWSD_TOPK patterns exist).
+ * Asynchronous.
+ */
+MPWSD_API int mpwsd_score_topk(mpwsd_code *code, int score_mode, const float *y_dev, int64_t B, const int32_t *frame_dev,
+                     const uint64_t *cw_dev, int64_t M, float *topk_val_dev, int32_t *topk_idx_dev, void *stream);
+
+/* Wait for `stream`, then report (and clear) a device-side timeout recorded
+ * by earlier work of this handle: MPWSD_OK or MPWSD_ETIMEOUT. */
+MPWSD_API int mpwsd_sync(mpwsd_code *code, void *stream);
+
+/* Read (synchronising the device) / reset the handle's counters. */
+MPWSD_API int mpwsd_stats_get(mpwsd_code *code, mpwsd_stats *out);
+MPWSD_API int mpwsd_stats_reset(mpwsd_code *code);
+
+/*
+ * mpwsd_enumerate_codewords -- host helper that builds pattern sets: every
+ * codeword of the code defined by `frozen` whose Hamming weight is in
+ * weights[0..n_weights), in the order (weight ascending as listed in
+ * `weights`, which must be ascending; then message integer ascending, where
+ * the message integer reads the information bits with the lowest index as the
+ * most significant bit). Brute force over all 2^k messages (k <= 40).
+ * If out is NULL only *count is set; otherwise at most max_out codewords are
+ * written (MPWSD_EINVAL if more exist). Host memory only; synchronous.
+ */
+MPWSD_API int mpwsd_enumerate_codewords(int n, const uint8_t *frozen, const int *weights, int n_weights, uint64_t *out,
+                              int64_t max_out, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPWSD_H */

@@ -14,6 +14,7 @@ through ctypes with numpy arrays. What each function restates:
 * ``enumerate_codewords``, ``weight_distribution`` -- S_r(0), Sec. II-C, Eqs. (1)-(3)
 * ``mpwsd`` -- Algorithm 1 with the filter of Eq. (5), Sec. III-B/C
 * ``decode`` -- the two-stage decoder, Sec. III
+* ``gains`` -- the correlation gain G_k(c) of Eq. (5) for every pattern
 * ``ml`` -- brute-force maximum-likelihood decoding (the optimality reference, Sec. IV-A)
 """
 from __future__ import annotations
@@ -70,6 +71,7 @@ def _load():
             "or_decode": (i32, [P, P, i64, i32, i32, i32, i32, i32, P, P, P, P, P]),
             "or_mpwsd": (None, [P, P, P, i32, i32, P, P, P, P, P]),
             "or_ml": (None, [P, P, P, P]),
+            "or_gains": (None, [P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -225,6 +227,14 @@ class Code:
         _load().or_mpwsd(self._h, _ptr(y), _ptr(a), int(a.shape[0]), T, _ptr(out), ctypes.byref(it),
                          ctypes.byref(gap), ctypes.byref(ev), ctypes.byref(fk))
         return dict(cw=out, iters=it.value, min_gap=gap.value, evals=ev.value, final_k=fk.value)
+
+    def gains(self, y, cw) -> np.ndarray:
+        """G(p) of Eq. (5) for every pattern around the centre cw (n bytes)."""
+        y = np.ascontiguousarray(y, np.float64)
+        cw = np.ascontiguousarray(cw, np.uint8)
+        G = np.zeros(max(self.patterns.shape[0], 1), np.float64)
+        _load().or_gains(self._h, _ptr(y), _ptr(cw), _ptr(G))
+        return G[:self.patterns.shape[0]]
 
     def ml(self, y):
         y = np.ascontiguousarray(y, np.float64)

@@ -658,6 +658,17 @@ void or_mpwsd(const or_code *c, const double *y, const uint8_t *anchors, int cou
     *final_k = info.final_k;
 }
 
+/* Correlation gains of Eq. (5) for every pattern around centre cw:
+ * G(p) = sum_{j in supp p} -2 y_j xhat_j, xhat = 1 - 2 cw. FP64, exact on the grid. */
+void or_gains(const or_code *c, const double *y, const uint8_t *cw, double *G) {
+    for (int64_t p = 0; p < c->P; p++) {
+        const int *sp = c->pat_supp + (size_t)p * c->n;
+        double g = 0.0;
+        for (int t = 0; t < c->pat_w[p]; t++) g += -2.0 * y[sp[t]] * (1.0 - 2.0 * cw[sp[t]]);
+        G[p] = g;
+    }
+}
+
 /* Brute-force ML: argmin ||y - x(c)||^2 over all 2^k codewords (ties keep the
  * smallest message integer a, with info bit t at bit t of a). Codewords are
  * formed by XOR of bit-packed generator rows; the distance is computed from

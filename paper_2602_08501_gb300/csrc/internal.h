@@ -1,0 +1,118 @@
+// Internal declarations shared by the translation units of libmpwsd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mpwsd.h"
+
+namespace mpwsd {
+
+constexpr int kTopK = MPWSD_TOPK;
+constexpr int kGridShift = 19;            // y is read on the 2^-19 grid
+constexpr int kGridMax = (1 << 23) - 1;   // |round(y 2^19)| <= 2^23 - 1
+// Margin of the near-tie re-rank: every approximate score is within
+// kEpsScale * ||y||_1 of the exact one (bf16 hi+lo split: 2^-16 ||y||_1;
+// FP32 accumulation: < 2^-18 ||y||_1 for the kernels here), so any pattern
+// whose approximate score is within 2 eps of the approximate minimum may be
+// the exact minimum and is re-scored exactly.
+constexpr float kEpsScale = 1.0f / 16384.0f;  // 2^-14
+
+// Trajectory state bits
+constexpr uint32_t kTrajHopsMask = 0xffu;
+constexpr uint32_t kTrajRescan = 1u << 8;
+constexpr uint32_t kTrajValid = 1u << 9;
+
+// Device-side counters (accumulated by the kernels; read by mpwsd_stats_get).
+struct DevStats {
+    unsigned long long frames;
+    unsigned long long stage2_frames;
+    unsigned long long trajectories;
+    unsigned long long pattern_evals;
+    unsigned long long rerank_candidates;
+    unsigned long long rescans;
+    unsigned long long hops;
+    unsigned long long error;  // nonzero after a bounded device wait gave up
+};
+
+// Per-decode device scratch. All arrays are sized for (max_B, max_L).
+struct Workspace {
+    int64_t max_B = 0;
+    int max_L = 0;
+    int device = -1;
+    void *base = nullptr;       // one cudaMalloc holding everything below
+    size_t bytes = 0;
+    int *counters = nullptr;    // [0] = failing frames F, [1 + i] = active rows before iteration i (i <= T), [32 + i] = rescan rows in iteration i
+    int *slot_frame = nullptr;  // F: frame index of each failing-frame slot
+    float *slot_l1 = nullptr;   // F: ||y||_1 of the frame
+    uint64_t *traj_cw = nullptr;  // F*L x W: trajectory centres
+    double *traj_D = nullptr;     // F*L: -sum_j y_j x_j (ED = ||y||^2 + n + 2 D)
+    uint32_t *traj_state = nullptr;  // F*L: hops | rescan | valid
+    int *act[2] = {nullptr, nullptr};  // active trajectory lists (ping-pong)
+    int *rescan_rows = nullptr;   // rows whose top-K overflowed the margin
+    float *topk_val = nullptr;    // F*L x K
+    int *topk_idx = nullptr;      // F*L x K
+};
+
+// Everything the kernels need to know about a loaded code.
+struct CodeDev {
+    int n = 0, W = 0, m = 0, k = 0, k_info = 0, crc_len = 0;
+    uint32_t crc_poly = 0;
+    int64_t P = 0;
+    uint64_t frozen_lo = 0, frozen_hi = 0;
+    int rm_spec = 0;              // 0 = generic frozen set, else a compiled Reed-Muller specialisation id
+    bool trailing_frozen = false; // a frozen leaf follows the last information leaf
+    int w_max = 0;                // largest pattern weight
+    int wq_max = 0;               // support words per pattern (4 indices per word)
+    // device arrays
+    uint64_t *pat_bits = nullptr;   // P x W
+    uint32_t *pat_supp = nullptr;   // P x wq_max, 4 uint8 indices per word, padded with index n
+    uint16_t *pat_tiles = nullptr;  // ceil(P/256) tiles of 256 x n bf16, smem image (128B swizzle, K-major)
+    int64_t n_tiles = 0;
+    uint64_t *crc_masks = nullptr;  // crc_len x W, codeword domain: syndrome bit b = parity(c & mask_b)
+    DevStats *stats = nullptr;
+    int num_sms = 0;
+};
+
+struct SclArgs {
+    const float *y;
+    int64_t B;
+    int L;
+    int mode;            // 0 = decode (CRC + compaction), 1 = list output
+    int rule;            // MPWSD_RULE_*
+    int use_crc;         // stage-1 early exit enabled
+    // decode mode
+    uint64_t *cw_out;
+    uint16_t *flags_out;
+    Workspace ws;
+    // list mode
+    uint64_t *list_cw;
+    int64_t *list_pm;
+};
+
+struct ScoreArgs {
+    const float *y;
+    const int *rows;          // active list: trajectory ids (decode) or row ids (direct)
+    const int *n_rows_dev;    // device count of rows (nullptr: use n_rows)
+    int64_t n_rows;
+    const uint64_t *cw;       // centre of trajectory id t at cw + t*W
+    const int *slot_frame;    // frame of trajectory id t = slot_frame[t / L] (decode) ...
+    const int32_t *row_frame; // ... or frame of row r = row_frame[r] (direct)
+    int L;
+    float *topk_val;          // row-indexed
+    int *topk_idx;
+    unsigned long long *evals; // stats counter (may be null)
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_scl(const CodeDev &c, const SclArgs &a, cudaStream_t s);
+cudaError_t launch_score_fp32(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
+cudaError_t launch_score_tc(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
+bool score_tc_supported(const CodeDev &c);
+int rm_specialisation(int n, uint64_t lo, uint64_t hi);
+cudaError_t launch_hop(const CodeDev &c, const Workspace &ws, int iter, int L, const float *y, cudaStream_t s);
+cudaError_t launch_rescan(const CodeDev &c, const Workspace &ws, int iter, int L, const float *y, cudaStream_t s);
+cudaError_t launch_final(const CodeDev &c, const Workspace &ws, int L, int T, int64_t B, uint64_t *cw_out, uint16_t *flags_out,
+                         cudaStream_t s);
+
+}  // namespace mpwsd

@@ -1,0 +1,641 @@
+// C ABI of libmpwsd (declared in include/mpwsd.h): argument validation, the
+// device image of a code (Sec. II-B code model, Sec. II-C pattern set), the
+// per-decode workspaces, and the launch sequence of the two-stage decoder
+// (Sec. III-A stage 1, Sec. III-B Algorithm 1 stage 2). Host code only;
+// every arithmetic step of a decode runs in the CUDA kernels.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <unordered_set>
+#include <vector>
+
+#include "internal.h"
+
+using namespace mpwsd;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int status, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) return fail(MPWSD_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(MPWSD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Test hook: MPWSD_TEST_FAIL_ALLOC=k makes the k-th device allocation of the
+// process (counted from 1) report out-of-memory without allocating.
+std::atomic<long> g_alloc_count{0};
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+    const long k = ++g_alloc_count;
+    const char *env = getenv("MPWSD_TEST_FAIL_ALLOC");
+    if (env && atol(env) == k) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes == 0 ? 16 : bytes);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Row i of [[1,0],[1,1]]^{(x)m} has ones exactly at the submasks j of i.
+inline bool kron_entry(int i, int j) { return (i & j) == j; }
+
+uint16_t f32_to_bf16_bits(float f) {  // exact for 0.0 and 1.0, the only values used
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return (uint16_t)(u >> 16);
+}
+
+}  // namespace
+
+struct mpwsd_workspace {
+    Workspace w;
+};
+
+struct mpwsd_code {
+    CodeDev d;
+    std::vector<int> info;  // non-frozen indices, ascending
+    mpwsd_workspace *default_ws = nullptr;
+    std::atomic<long long> launches{0};
+    std::mutex mu;
+};
+
+extern "C" const char *mpwsd_strerror(int status) {
+    switch (status) {
+        case MPWSD_OK: return "MPWSD_OK";
+        case MPWSD_EINVAL: return "MPWSD_EINVAL: invalid argument";
+        case MPWSD_ENOMEM: return "MPWSD_ENOMEM: out of memory";
+        case MPWSD_ECUDA: return "MPWSD_ECUDA: CUDA error";
+        case MPWSD_ETIMEOUT: return "MPWSD_ETIMEOUT: device-side wait timed out";
+        case MPWSD_EUNSUPPORTED: return "MPWSD_EUNSUPPORTED: not supported by this build";
+        default: return "unknown mpwsd status";
+    }
+}
+
+extern "C" const char *mpwsd_last_error(void) { return g_err.c_str(); }
+
+static void free_code_device(CodeDev &d) {
+    cudaFree(d.pat_bits);
+    cudaFree(d.pat_supp);
+    cudaFree(d.pat_tiles);
+    cudaFree(d.crc_masks);
+    cudaFree(d.stats);
+    d.pat_bits = nullptr;
+    d.pat_supp = nullptr;
+    d.pat_tiles = nullptr;
+    d.crc_masks = nullptr;
+    d.stats = nullptr;
+}
+
+extern "C" int mpwsd_load_code(int n, const uint8_t *G, const uint8_t *frozen, int k_info, uint32_t crc_poly,
+                               int crc_len, const uint64_t *patterns, int64_t n_patterns, mpwsd_code **out) {
+    if (!out) return fail(MPWSD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n != 32 && n != 64 && n != 128) return fail(MPWSD_EINVAL, "n = %d: must be 32, 64 or 128", n);
+    if (!frozen) return fail(MPWSD_EINVAL, "frozen is NULL");
+    if (!patterns || n_patterns < 1 || n_patterns > 0x7fffffffLL)
+        return fail(MPWSD_EINVAL, "need 1 <= n_patterns < 2^31 and a pattern array");
+    if (crc_len < 0 || crc_len > 32) return fail(MPWSD_EINVAL, "crc_len = %d: must be 0..32", crc_len);
+    if (crc_len < 32 && (crc_poly >> crc_len) != 0) return fail(MPWSD_EINVAL, "crc_poly has bits above crc_len");
+    const int W = (n + 63) / 64;
+    int m = 0;
+    while ((1 << m) < n) ++m;
+    std::vector<int> info;
+    for (int i = 0; i < n; ++i) {
+        if (frozen[i] > 1) return fail(MPWSD_EINVAL, "frozen[%d] = %d: must be 0 or 1", i, frozen[i]);
+        if (!frozen[i]) info.push_back(i);
+    }
+    const int k = (int)info.size();
+    if (k < 1) return fail(MPWSD_EINVAL, "no information positions");
+    if (k_info < 1 || k_info + crc_len != k)
+        return fail(MPWSD_EINVAL, "k_info (%d) + crc_len (%d) must equal the %d information positions", k_info, crc_len, k);
+    if (G) {
+        for (int t = 0; t < k; ++t)
+            for (int j = 0; j < n; ++j)
+                if ((G[(size_t)t * n + j] != 0) != kron_entry(info[t], j))
+                    return fail(MPWSD_EINVAL, "G row %d differs from row %d of the Arikan kernel power", t, info[t]);
+    }
+    // patterns: nonzero, within n bits, codewords (u = p F zero on frozen), distinct
+    std::vector<uint8_t> frz(frozen, frozen + n);
+    int w_max = 0;
+    {
+        std::unordered_set<std::string> seen;
+        seen.reserve((size_t)n_patterns * 2);
+        for (int64_t p = 0; p < n_patterns; ++p) {
+            const uint64_t *pw = patterns + p * W;
+            if (n < 64 && (pw[0] >> n) != 0) return fail(MPWSD_EINVAL, "pattern %lld has bits beyond n", (long long)p);
+            int w = 0;
+            for (int q = 0; q < W; ++q) w += __builtin_popcountll(pw[q]);
+            if (w == 0) return fail(MPWSD_EINVAL, "pattern %lld is the zero word", (long long)p);
+            w_max = std::max(w_max, w);
+            // u_i = sum_j c_j F[j][i] = parity of c restricted to supersets of i
+            for (int i = 0; i < n; ++i) {
+                if (!frz[i]) continue;
+                int par = 0;
+                for (int q = 0; q < W; ++q) {
+                    uint64_t sup = 0;  // positions j (in word q) with i a submask of j
+                    for (int b = 0; b < 64 && q * 64 + b < n; ++b)
+                        if (kron_entry(q * 64 + b, i)) sup |= 1ull << b;
+                    par ^= __builtin_popcountll(pw[q] & sup) & 1;
+                }
+                if (par) return fail(MPWSD_EINVAL, "pattern %lld is not a codeword (frozen u_%d = 1)", (long long)p, i);
+            }
+            if (!seen.insert(std::string((const char *)pw, (size_t)W * 8)).second)
+                return fail(MPWSD_EINVAL, "pattern %lld repeats an earlier pattern", (long long)p);
+        }
+    }
+
+    mpwsd_code *c = new (std::nothrow) mpwsd_code();
+    if (!c) return fail(MPWSD_ENOMEM, "host allocation");
+    CodeDev &d = c->d;
+    c->info = info;
+    d.n = n;
+    d.W = W;
+    d.m = m;
+    d.k = k;
+    d.k_info = k_info;
+    d.crc_len = crc_len;
+    d.crc_poly = crc_poly;
+    d.P = n_patterns;
+    for (int i = 0; i < n; ++i)
+        if (frozen[i]) {
+            if (i < 64)
+                d.frozen_lo |= 1ull << i;
+            else
+                d.frozen_hi |= 1ull << (i - 64);
+        }
+    d.rm_spec = rm_specialisation(n, d.frozen_lo, d.frozen_hi);
+    d.trailing_frozen = info.back() != n - 1;
+    d.w_max = w_max;
+    d.wq_max = (w_max + 3) / 4;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    e = cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaDeviceGetAttribute");
+    }
+
+    // host images
+    std::vector<uint32_t> supp((size_t)n_patterns * d.wq_max, 0);
+    for (int64_t p = 0; p < n_patterns; ++p) {
+        uint8_t idx[128];
+        int w = 0;
+        for (int j = 0; j < n; ++j)
+            if ((patterns[p * W + j / 64] >> (j % 64)) & 1ull) idx[w++] = (uint8_t)j;
+        for (; w < d.wq_max * 4; ++w) idx[w] = (uint8_t)n;  // pad: reads the zero slot
+        for (int q = 0; q < d.wq_max; ++q)
+            supp[(size_t)p * d.wq_max + q] = (uint32_t)idx[4 * q] | ((uint32_t)idx[4 * q + 1] << 8) |
+                                             ((uint32_t)idx[4 * q + 2] << 16) | ((uint32_t)idx[4 * q + 3] << 24);
+    }
+    // bf16 0/1 pattern tiles, 256 patterns x n per tile, laid out as the shared
+    // memory image a K-major 128-byte-swizzled UMMA operand expects: for each
+    // 64-element K chunk, rows of 128 B grouped in 1024-B atoms, 16-B unit u of
+    // row r stored at unit u ^ (r % 8).
+    d.n_tiles = (n_patterns + 255) / 256;
+    const int kchunks = n / 64 > 0 ? n / 64 : 1;
+    const size_t tile_elems = (size_t)256 * kchunks * 64;
+    std::vector<uint16_t> tiles;
+    if (n >= 64) {
+        tiles.assign((size_t)d.n_tiles * tile_elems, 0);
+        const uint16_t one = f32_to_bf16_bits(1.0f);
+        for (int64_t p = 0; p < n_patterns; ++p) {
+            const int64_t tile = p / 256;
+            const int r = (int)(p % 256);
+            for (int j = 0; j < n; ++j) {
+                if (!((patterns[p * W + j / 64] >> (j % 64)) & 1ull)) continue;
+                const int kc = j / 64, e64 = j % 64;
+                const int unit = e64 / 8, within = e64 % 8;
+                const size_t off = (size_t)tile * tile_elems + (size_t)kc * 256 * 64 + (size_t)r * 64 +
+                                   (size_t)((unit ^ (r % 8)) * 8 + within);
+                tiles[off] = one;
+            }
+        }
+    }
+    // CRC: parity matrix by long division of the unit messages, then the
+    // syndrome masks moved to the codeword domain (u = c F, F an involution).
+    std::vector<uint64_t> masks((size_t)std::max(crc_len, 1) * W, 0);
+    for (int b = 0; b < crc_len; ++b) {
+        std::vector<uint8_t> inset(n, 0);  // M_b over u indices
+        for (int t = 0; t < k_info; ++t) {
+            // remainder of x^(k_info - 1 - t + crc_len) mod g(x)
+            uint64_t val = 1;
+            const uint64_t top = 1ull << crc_len;
+            for (int s = 0; s < k_info - 1 - t + crc_len; ++s) {
+                val <<= 1;
+                if (val & top) val ^= top | crc_poly;
+            }
+            if ((val >> (crc_len - 1 - b)) & 1ull) inset[info[t]] = 1;
+        }
+        inset[info[k_info + b]] = 1;
+        for (int j = 0; j < n; ++j) {
+            int par = 0;
+            for (int i = 0; i < n; ++i)
+                if (inset[i] && kron_entry(j, i)) par ^= 1;
+            if (par) masks[(size_t)b * W + j / 64] |= 1ull << (j % 64);
+        }
+    }
+    // device images
+    struct Up {
+        void **dst;
+        const void *src;
+        size_t bytes;
+    } ups[] = {
+        {(void **)&d.pat_bits, patterns, (size_t)n_patterns * W * 8},
+        {(void **)&d.pat_supp, supp.data(), supp.size() * 4},
+        {(void **)&d.pat_tiles, tiles.data(), tiles.size() * 2},
+        {(void **)&d.crc_masks, masks.data(), masks.size() * 8},
+    };
+    for (auto &u : ups) {
+        e = dev_alloc(u.dst, u.bytes);
+        if (e == cudaSuccess && u.bytes) e = cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free_code_device(d);
+            delete c;
+            return cuda_fail(e, "uploading the code");
+        }
+    }
+    e = dev_alloc((void **)&d.stats, sizeof(DevStats));
+    if (e == cudaSuccess) e = cudaMemset(d.stats, 0, sizeof(DevStats));
+    if (e != cudaSuccess) {
+        free_code_device(d);
+        delete c;
+        return cuda_fail(e, "allocating counters");
+    }
+    *out = c;
+    return MPWSD_OK;
+}
+
+extern "C" int mpwsd_code_info(const mpwsd_code *code, int *n, int *k, int64_t *n_patterns, int *max_w) {
+    if (!code) return fail(MPWSD_EINVAL, "code is NULL");
+    if (n) *n = code->d.n;
+    if (k) *k = code->d.k;
+    if (n_patterns) *n_patterns = code->d.P;
+    if (max_w) *max_w = code->d.w_max;
+    return MPWSD_OK;
+}
+
+// ---- workspaces -------------------------------------------------------------
+
+static size_t ws_layout(const CodeDev &d, int64_t max_B, int max_L, Workspace *w) {
+    const int64_t M = max_B * max_L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    const size_t o_cnt = take(64 * sizeof(int));
+    const size_t o_sf = take((size_t)max_B * sizeof(int));
+    const size_t o_l1 = take((size_t)max_B * sizeof(float));
+    const size_t o_cw = take((size_t)M * d.W * 8);
+    const size_t o_D = take((size_t)M * 8);
+    const size_t o_st = take((size_t)M * 4);
+    const size_t o_a0 = take((size_t)M * 4);
+    const size_t o_a1 = take((size_t)M * 4);
+    const size_t o_rs = take((size_t)M * 4);
+    const size_t o_tv = take((size_t)M * kTopK * 4);
+    const size_t o_ti = take((size_t)M * kTopK * 4);
+    if (w && w->base) {
+        char *b = (char *)w->base;
+        w->counters = (int *)(b + o_cnt);
+        w->slot_frame = (int *)(b + o_sf);
+        w->slot_l1 = (float *)(b + o_l1);
+        w->traj_cw = (uint64_t *)(b + o_cw);
+        w->traj_D = (double *)(b + o_D);
+        w->traj_state = (uint32_t *)(b + o_st);
+        w->act[0] = (int *)(b + o_a0);
+        w->act[1] = (int *)(b + o_a1);
+        w->rescan_rows = (int *)(b + o_rs);
+        w->topk_val = (float *)(b + o_tv);
+        w->topk_idx = (int *)(b + o_ti);
+    }
+    return off;
+}
+
+extern "C" int mpwsd_workspace_bytes(const mpwsd_code *code, int64_t max_B, int max_L, size_t *bytes) {
+    if (!code || !bytes) return fail(MPWSD_EINVAL, "NULL argument");
+    if (max_B < 1 || max_L < 1 || max_L > MPWSD_MAX_L) return fail(MPWSD_EINVAL, "need max_B >= 1, 1 <= max_L <= 32");
+    if (max_B * max_L > 0x7fffffffLL) return fail(MPWSD_EINVAL, "max_B * max_L must stay below 2^31");
+    *bytes = ws_layout(code->d, max_B, max_L, nullptr);
+    return MPWSD_OK;
+}
+
+extern "C" int mpwsd_workspace_create(const mpwsd_code *code, int64_t max_B, int max_L, mpwsd_workspace **out) {
+    if (!out) return fail(MPWSD_EINVAL, "out is NULL");
+    *out = nullptr;
+    size_t bytes = 0;
+    int st = mpwsd_workspace_bytes(code, max_B, max_L, &bytes);
+    if (st) return st;
+    mpwsd_workspace *ws = new (std::nothrow) mpwsd_workspace();
+    if (!ws) return fail(MPWSD_ENOMEM, "host allocation");
+    cudaError_t e = dev_alloc(&ws->w.base, bytes);
+    if (e != cudaSuccess) {
+        delete ws;
+        cudaGetLastError();  // clear the sticky-free allocation error
+        return cuda_fail(e, "workspace allocation");
+    }
+    ws->w.bytes = bytes;
+    ws->w.max_B = max_B;
+    ws->w.max_L = max_L;
+    cudaGetDevice(&ws->w.device);
+    ws_layout(code->d, max_B, max_L, &ws->w);
+    *out = ws;
+    return MPWSD_OK;
+}
+
+extern "C" void mpwsd_workspace_free(mpwsd_workspace *ws) {
+    if (!ws) return;
+    cudaDeviceSynchronize();
+    cudaFree(ws->w.base);
+    delete ws;
+}
+
+extern "C" void mpwsd_free_code(mpwsd_code *code) {
+    if (!code) return;
+    cudaDeviceSynchronize();
+    mpwsd_workspace_free(code->default_ws);
+    free_code_device(code->d);
+    delete code;
+}
+
+// ---- decode -----------------------------------------------------------------
+
+static int check_opts(const mpwsd_opts *opts, mpwsd_opts *o) {
+    memset(o, 0, sizeof(*o));
+    if (!opts) return MPWSD_OK;
+    *o = *opts;
+    if (o->score_mode != MPWSD_SCORE_BF16X2 && o->score_mode != MPWSD_SCORE_FP32)
+        return fail(MPWSD_EINVAL, "score_mode = %d", o->score_mode);
+    if (o->stage1_rule != MPWSD_RULE_TOP1 && o->stage1_rule != MPWSD_RULE_ANY)
+        return fail(MPWSD_EINVAL, "stage1_rule = %d", o->stage1_rule);
+    for (int i = 0; i < 5; ++i)
+        if (o->reserved[i]) return fail(MPWSD_EINVAL, "reserved option fields must be zero");
+    return MPWSD_OK;
+}
+
+static int check_device(const mpwsd_code *code) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    (void)code;
+    return MPWSD_OK;
+}
+
+static cudaError_t launch_score(mpwsd_code *code, int mode, const ScoreArgs &a, cudaStream_t s) {
+    code->launches++;
+    if (mode == MPWSD_SCORE_FP32) return launch_score_fp32(code->d, a, s);
+    return launch_score_tc(code->d, a, s);
+}
+
+static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int64_t B, int L, int T,
+                       const mpwsd_opts &o, uint64_t *cw_dev, uint16_t *flags_dev, cudaStream_t s) {
+    CodeDev &d = code->d;
+    cudaError_t e = cudaMemsetAsync(ws.counters, 0, 64 * sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    SclArgs sa{};
+    sa.y = y_dev;
+    sa.B = B;
+    sa.L = L;
+    sa.mode = 0;
+    sa.rule = o.stage1_rule;
+    sa.use_crc = d.crc_len > 0 && !o.always_on;
+    sa.cw_out = cw_dev;
+    sa.flags_out = flags_dev;
+    sa.ws = ws;
+    code->launches++;
+    e = launch_scl(d, sa, s);
+    if (e != cudaSuccess) return cuda_fail(e, "stage-1 launch");
+    for (int it = 0; it < T; ++it) {
+        ScoreArgs a{};
+        a.y = y_dev;
+        a.rows = ws.act[it & 1];
+        a.n_rows_dev = ws.counters + 1 + it;
+        a.cw = ws.traj_cw;
+        a.slot_frame = ws.slot_frame;
+        a.L = L;
+        a.topk_val = ws.topk_val;
+        a.topk_idx = ws.topk_idx;
+        e = launch_score(code, o.score_mode, a, s);
+        if (e != cudaSuccess) return cuda_fail(e, "scoring launch");
+        code->launches += 2;
+        e = launch_hop(d, ws, it, L, y_dev, s);
+        if (e == cudaSuccess) e = launch_rescan(d, ws, it, L, y_dev, s);
+        if (e != cudaSuccess) return cuda_fail(e, "hop launch");
+    }
+    code->launches++;
+    e = launch_final(d, ws, L, T, B, cw_dev, flags_dev, s);
+    if (e != cudaSuccess) return cuda_fail(e, "final launch");
+    return MPWSD_OK;
+}
+
+static int check_decode_args(mpwsd_code *code, const float *y_dev, int64_t B, int L, int T, const mpwsd_opts *opts,
+                             uint64_t *cw_dev, uint16_t *flags_dev, mpwsd_opts *o) {
+    if (!code) return fail(MPWSD_EINVAL, "code is NULL");
+    if (B < 0) return fail(MPWSD_EINVAL, "B < 0");
+    if (L < 1 || L > MPWSD_MAX_L) return fail(MPWSD_EINVAL, "L = %d: must be 1..%d", L, MPWSD_MAX_L);
+    if (T < 1 || T > MPWSD_MAX_T) return fail(MPWSD_EINVAL, "T = %d: must be 1..%d", T, MPWSD_MAX_T);
+    if (B > 0 && (!y_dev || !cw_dev || !flags_dev)) return fail(MPWSD_EINVAL, "NULL buffer");
+    if (B > 0x7fffffffLL / L) return fail(MPWSD_EINVAL, "B * L must stay below 2^31");
+    int st = check_opts(opts, o);
+    if (st) return st;
+    if (o->score_mode == MPWSD_SCORE_BF16X2 && !score_tc_supported(code->d))
+        return fail(MPWSD_EUNSUPPORTED, "BF16X2 tensor-core scoring needs n = 64 or 128");
+    return check_device(code);
+}
+
+extern "C" int mpwsd_decode_ws(mpwsd_code *code, mpwsd_workspace *ws, const float *y_dev, int64_t B, int L, int T,
+                               const mpwsd_opts *opts, uint64_t *cw_dev, uint16_t *flags_dev, void *stream) {
+    mpwsd_opts o;
+    int st = check_decode_args(code, y_dev, B, L, T, opts, cw_dev, flags_dev, &o);
+    if (st) return st;
+    if (!ws) return fail(MPWSD_EINVAL, "workspace is NULL");
+    if (B > ws->w.max_B || L > ws->w.max_L)
+        return fail(MPWSD_EINVAL, "B = %lld, L = %d exceed the workspace (%lld, %d)", (long long)B, L,
+                    (long long)ws->w.max_B, ws->w.max_L);
+    if (B == 0) return MPWSD_OK;
+    return decode_impl(code, ws->w, y_dev, B, L, T, o, cw_dev, flags_dev, (cudaStream_t)stream);
+}
+
+extern "C" int mpwsd_decode(mpwsd_code *code, const float *y_dev, int64_t B, int L, int T, const mpwsd_opts *opts,
+                            uint64_t *cw_dev, uint16_t *flags_dev, void *stream) {
+    mpwsd_opts o;
+    int st = check_decode_args(code, y_dev, B, L, T, opts, cw_dev, flags_dev, &o);
+    if (st) return st;
+    if (B == 0) return MPWSD_OK;
+    std::lock_guard<std::mutex> lk(code->mu);
+    mpwsd_workspace *ws = code->default_ws;
+    if (!ws || ws->w.max_B < B || ws->w.max_L < L) {
+        const int64_t nb = std::max<int64_t>(B, ws ? ws->w.max_B : 0);
+        const int nl = std::max(L, ws ? ws->w.max_L : 0);
+        mpwsd_workspace *nw = nullptr;
+        st = mpwsd_workspace_create(code, nb, nl, &nw);
+        if (st) return st;
+        mpwsd_workspace_free(ws);
+        code->default_ws = ws = nw;
+    }
+    return decode_impl(code, ws->w, y_dev, B, L, T, o, cw_dev, flags_dev, (cudaStream_t)stream);
+}
+
+extern "C" int mpwsd_stage1_list(mpwsd_code *code, const float *y_dev, int64_t B, int L, uint64_t *list_cw_dev,
+                                 int64_t *list_pm_dev, void *stream) {
+    if (!code) return fail(MPWSD_EINVAL, "code is NULL");
+    if (B < 0 || L < 1 || L > MPWSD_MAX_L) return fail(MPWSD_EINVAL, "need B >= 0 and 1 <= L <= 32");
+    if (B > 0 && (!y_dev || !list_cw_dev || !list_pm_dev)) return fail(MPWSD_EINVAL, "NULL buffer");
+    if (B == 0) return MPWSD_OK;
+    SclArgs sa{};
+    sa.y = y_dev;
+    sa.B = B;
+    sa.L = L;
+    sa.mode = 1;
+    sa.list_cw = list_cw_dev;
+    sa.list_pm = list_pm_dev;
+    code->launches++;
+    cudaError_t e = launch_scl(code->d, sa, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stage-1 launch");
+    return MPWSD_OK;
+}
+
+extern "C" int mpwsd_score_topk(mpwsd_code *code, int score_mode, const float *y_dev, int64_t B,
+                                const int32_t *frame_dev, const uint64_t *cw_dev, int64_t M, float *topk_val_dev,
+                                int32_t *topk_idx_dev, void *stream) {
+    if (!code) return fail(MPWSD_EINVAL, "code is NULL");
+    if (score_mode != MPWSD_SCORE_BF16X2 && score_mode != MPWSD_SCORE_FP32)
+        return fail(MPWSD_EINVAL, "score_mode = %d", score_mode);
+    if (score_mode == MPWSD_SCORE_BF16X2 && !score_tc_supported(code->d))
+        return fail(MPWSD_EUNSUPPORTED, "BF16X2 tensor-core scoring needs n = 64 or 128");
+    if (M < 0 || B < 0 || M > 0x7fffffffLL) return fail(MPWSD_EINVAL, "bad sizes");
+    if (M > 0 && (!y_dev || !frame_dev || !cw_dev || !topk_val_dev || !topk_idx_dev))
+        return fail(MPWSD_EINVAL, "NULL buffer");
+    if (M == 0) return MPWSD_OK;
+    ScoreArgs a{};
+    a.y = y_dev;
+    a.rows = nullptr;
+    a.n_rows_dev = nullptr;
+    a.n_rows = M;
+    a.cw = cw_dev;
+    a.row_frame = frame_dev;
+    a.L = 1;
+    a.topk_val = topk_val_dev;
+    a.topk_idx = topk_idx_dev;
+    cudaError_t e = launch_score(code, score_mode, a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "scoring launch");
+    return MPWSD_OK;
+}
+
+extern "C" int mpwsd_sync(mpwsd_code *code, void *stream) {
+    if (!code) return fail(MPWSD_EINVAL, "code is NULL");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    unsigned long long err = 0;
+    e = cudaMemcpy(&err, &code->d.stats->error, sizeof(err), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the error word");
+    if (err) {
+        cudaMemset(&code->d.stats->error, 0, sizeof(err));
+        return fail(MPWSD_ETIMEOUT, "a bounded device-side wait gave up (code %llu)", err);
+    }
+    return MPWSD_OK;
+}
+
+extern "C" int mpwsd_stats_get(mpwsd_code *code, mpwsd_stats *out) {
+    if (!code || !out) return fail(MPWSD_EINVAL, "NULL argument");
+    cudaError_t e = cudaDeviceSynchronize();
+    DevStats ds;
+    if (e == cudaSuccess) e = cudaMemcpy(&ds, code->d.stats, sizeof(ds), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading counters");
+    out->frames = (int64_t)ds.frames;
+    out->stage2_frames = (int64_t)ds.stage2_frames;
+    out->trajectories = (int64_t)ds.trajectories;
+    out->pattern_evals = (int64_t)ds.pattern_evals;
+    out->rerank_candidates = (int64_t)ds.rerank_candidates;
+    out->rescans = (int64_t)ds.rescans;
+    out->hops = (int64_t)ds.hops;
+    out->kernel_launches = code->launches.load();
+    return MPWSD_OK;
+}
+
+extern "C" int mpwsd_stats_reset(mpwsd_code *code) {
+    if (!code) return fail(MPWSD_EINVAL, "code is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemset(code->d.stats, 0, sizeof(DevStats));
+    if (e != cudaSuccess) return cuda_fail(e, "resetting counters");
+    code->launches = 0;
+    return MPWSD_OK;
+}
+
+// ---- host pattern enumeration ------------------------------------------------
+
+extern "C" int mpwsd_enumerate_codewords(int n, const uint8_t *frozen, const int *weights, int n_weights,
+                                         uint64_t *out, int64_t max_out, int64_t *count) {
+    if (n != 32 && n != 64 && n != 128) return fail(MPWSD_EINVAL, "n = %d: must be 32, 64 or 128", n);
+    if (!frozen || !weights || n_weights < 1 || !count) return fail(MPWSD_EINVAL, "NULL argument");
+    for (int i = 0; i < n_weights; ++i) {
+        if (weights[i] < 1 || weights[i] > n) return fail(MPWSD_EINVAL, "weight %d out of range", weights[i]);
+        if (i && weights[i] <= weights[i - 1]) return fail(MPWSD_EINVAL, "weights must be strictly ascending");
+    }
+    std::vector<int> info;
+    for (int i = 0; i < n; ++i)
+        if (!frozen[i]) info.push_back(i);
+    const int k = (int)info.size();
+    if (k < 1 || k > 40) return fail(MPWSD_EINVAL, "k = %d: enumeration supports 1..40", k);
+    const int W = (n + 63) / 64;
+    // Gray-code walk: bit b of the message integer a is information index
+    // info[k-1-b] (lowest index = most significant bit); each step XORs one row.
+    std::vector<uint64_t> row((size_t)k * 2, 0);
+    for (int b = 0; b < k; ++b) {
+        const int i = info[k - 1 - b];
+        for (int j = 0; j < n; ++j)
+            if (kron_entry(i, j)) row[(size_t)b * 2 + j / 64] |= 1ull << (j % 64);
+    }
+    int wclass[129];
+    for (int w = 0; w <= 128; ++w) wclass[w] = -1;
+    for (int i = 0; i < n_weights; ++i) wclass[weights[i]] = i;
+    struct Rec {
+        int cls;
+        uint64_t a;
+        uint64_t c0, c1;
+    };
+    std::vector<Rec> recs;
+    uint64_t c0 = 0, c1 = 0;
+    const uint64_t total = 1ull << k;
+    for (uint64_t s = 1; s < total; ++s) {
+        const int b = __builtin_ctzll(s);
+        c0 ^= row[(size_t)b * 2];
+        c1 ^= row[(size_t)b * 2 + 1];
+        const int w = __builtin_popcountll(c0) + __builtin_popcountll(c1);
+        if (wclass[w] >= 0) recs.push_back({wclass[w], s ^ (s >> 1), c0, c1});
+    }
+    std::sort(recs.begin(), recs.end(), [](const Rec &x, const Rec &y) {
+        return x.cls != y.cls ? x.cls < y.cls : x.a < y.a;
+    });
+    *count = (int64_t)recs.size();
+    if (!out) return MPWSD_OK;
+    if ((int64_t)recs.size() > max_out) return fail(MPWSD_EINVAL, "%lld codewords do not fit in max_out", (long long)recs.size());
+    for (size_t i = 0; i < recs.size(); ++i) {
+        out[i * W] = recs[i].c0;
+        if (W > 1) out[i * W + 1] = recs[i].c1;
+    }
+    return MPWSD_OK;
+}

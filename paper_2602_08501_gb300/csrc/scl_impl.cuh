@@ -1,0 +1,375 @@
+#pragma once
+// Stage-1 kernel templates (included by the scl_*.cu instantiation units).
+//
+// Stage 1 of the two-stage decoder (Sec. III-A): batched min-sum SC-list
+// decoding on the Arikan transform, CRC check of the most reliable candidate
+// with early termination, and compaction of the failing frames into stage-2
+// trajectories (one per list entry = anchor, Algorithm 1 init).
+//
+// GPU mapping: one thread per list path, LW = next power of two >= L lanes per
+// frame, 32 / LW frames per warp. The SC schedule (which f / g updates run
+// before each leaf) does not depend on the data, so it is unrolled at compile
+// time and every LLR lives in a register. At an information leaf the 2|list|
+// children are ranked by the key (metric, parent position, bit) with warp
+// shuffles; each surviving child takes a lane and copies from its parent lane
+// only the state still needed later (LLR arrays of ancestors whose right
+// subtree is pending, left-subtree codewords of ancestors whose right subtree
+// is running). Integer LLRs: inputs on the 2^-19 grid are exact int32, path
+// metrics int64, so the list equals the FP64 formulation bit for bit.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace mpwsd {
+namespace scl_detail {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarpsPerBlock = 4;
+
+template <int X>
+struct Log2 {
+    static constexpr int v = 1 + Log2<X / 2>::v;
+};
+template <>
+struct Log2<1> {
+    static constexpr int v = 0;
+};
+
+constexpr int cpop(uint32_t x) { return x == 0 ? 0 : (int)(x & 1u) + cpop(x >> 1); }
+
+// Frozen mask of RM(r, m) in the Arikan form: row i is frozen iff its weight
+// 2^popcount(i) is below the minimum distance 2^(m-r).
+constexpr uint64_t rm_mask(int m, int r, int word) {
+    uint64_t v = 0;
+    for (int b = 0; b < 64; ++b) {
+        int i = word * 64 + b;
+        if (i < (1 << m) && cpop((uint32_t)i) < m - r) v |= 1ull << b;
+    }
+    return v;
+}
+
+struct FrozenRT {
+    static constexpr bool kConst = false;
+    uint64_t lo, hi;
+    template <int I>
+    __device__ __forceinline__ bool frozen() const {
+        if constexpr (I < 64)
+            return (lo >> I) & 1ull;
+        else
+            return (hi >> (I - 64)) & 1ull;
+    }
+};
+
+template <uint64_t LO, uint64_t HI>
+struct FrozenCT {
+    static constexpr bool kConst = true;
+    uint64_t lo, hi;  // unused, keeps the launch signature uniform
+    template <int I>
+    __device__ __forceinline__ static constexpr bool frozen() {
+        if constexpr (I < 64)
+            return (LO >> I) & 1ull;
+        else
+            return (HI >> (I - 64)) & 1ull;
+    }
+};
+
+template <int N>
+struct PathState {
+    int llr[N];                    // node of size S < N keeps its LLRs at [S, 2S)
+    uint64_t beta[Log2<N>::v];     // beta[log2 H]: codeword of the finished left child of size H
+    long long pm;                  // path metric, units of 2^-19
+};
+
+template <class FZ>
+struct SclCtx {
+    const int *ych;                // channel LLRs of this frame (shared memory)
+    unsigned long long *xchg;      // LW exchange slots of this frame (shared memory)
+    int lane;                      // lane within the frame's segment
+    int count;                     // current list size (uniform over the warp)
+    int L;
+    uint64_t root_cw[2];           // root codeword when n = 128
+    FZ fz;
+};
+
+__device__ __forceinline__ int minsum_f(int a, int b) {
+    int m = min(abs(a), abs(b));
+    return ((a ^ b) < 0) ? -m : m;  // sign(a) sign(b) min(|a|,|b|), sign(0) = +1
+}
+
+template <int N, int S>
+__device__ __forceinline__ int parent_llr(const int *ych, const PathState<N> &st, int k) {
+    if constexpr (S == N)
+        return ych[k];
+    else
+        return st.llr[S + k];
+}
+
+template <int N, int LW, int I, int S>
+__device__ __forceinline__ void clone_llr(PathState<N> &st, int par) {
+    if constexpr (S <= N / 2) {
+        if constexpr ((I & (S / 2)) == 0) {
+#pragma unroll
+            for (int k = 0; k < S; ++k) st.llr[S + k] = __shfl_sync(kFull, st.llr[S + k], par, LW);
+        }
+        clone_llr<N, LW, I, S * 2>(st, par);
+    }
+}
+
+template <int N, int LW, int I, int H>
+__device__ __forceinline__ void clone_beta(PathState<N> &st, int par) {
+    if constexpr (H <= N / 2) {
+        if constexpr ((I & H) != 0) st.beta[Log2<H>::v] = __shfl_sync(kFull, st.beta[Log2<H>::v], par, LW);
+        clone_beta<N, LW, I, H * 2>(st, par);
+    }
+}
+
+template <int N, int LW, class FZ, int I>
+__device__ __forceinline__ uint64_t info_leaf(SclCtx<FZ> &cx, PathState<N> &st) {
+    const int lam = st.llr[1];
+    const unsigned hd = lam < 0 ? 1u : 0u;
+    if constexpr (LW == 1) {
+        // one path: the child with the smaller key is always the hard decision
+        return hd;
+    } else {
+        const long long a = lam < 0 ? -(long long)lam : (long long)lam;
+        const bool valid = cx.lane < cx.count;
+        const unsigned long long base = ((unsigned long long)cx.lane << 1);
+        // key = (metric, parent position, bit); unique per child
+        const unsigned long long k0 = valid ? (((unsigned long long)st.pm << 6) | base | hd) : ~0ull;
+        const unsigned long long k1 = valid ? (((unsigned long long)(st.pm + a) << 6) | base | (hd ^ 1u)) : ~0ull;
+        int r0 = 0, r1 = 0;
+#pragma unroll 4
+        for (int s = 0; s < LW; ++s) {
+            const unsigned long long s0 = __shfl_sync(kFull, k0, s, LW);
+            const unsigned long long s1 = __shfl_sync(kFull, k1, s, LW);
+            r0 += (s0 < k0) + (s1 < k0);
+            r1 += (s0 < k1) + (s1 < k1);
+        }
+        const int nc = min(2 * cx.count, cx.L);
+        if (r0 < nc) cx.xchg[r0] = k0;
+        if (r1 < nc) cx.xchg[r1] = k1;
+        __syncwarp();
+        const bool keep = cx.lane < nc;
+        const unsigned long long kk = cx.xchg[keep ? cx.lane : 0];
+        __syncwarp();
+        const int par = keep ? (int)((kk >> 1) & 31ull) : cx.lane;
+        clone_llr<N, LW, I, 2>(st, par);
+        clone_beta<N, LW, I, 1>(st, par);
+        if (keep) st.pm = (long long)(kk >> 6);
+        cx.count = nc;
+        return keep ? (unsigned)(kk & 1ull) : 0u;
+    }
+}
+
+template <int N, int LW, class FZ, int I>
+__device__ __forceinline__ uint64_t leaf(SclCtx<FZ> &cx, PathState<N> &st) {
+    bool frz;
+    if constexpr (FZ::kConst)
+        frz = FZ::template frozen<I>();
+    else
+        frz = cx.fz.template frozen<I>();
+    if (frz) {
+        const int lam = st.llr[1];
+        if (lam < 0) st.pm -= lam;  // decided bit 0 disagrees with HD = 1
+        return 0;
+    }
+    return info_leaf<N, LW, FZ, I>(cx, st);
+}
+
+// Node of size S whose first leaf is OFF: returns the node's codeword (S <= 64)
+template <int N, int LW, class FZ, int S, int OFF>
+__device__ __forceinline__ uint64_t node(SclCtx<FZ> &cx, PathState<N> &st) {
+    if constexpr (S == 1) {
+        return leaf<N, LW, FZ, OFF>(cx, st);
+    } else {
+        constexpr int H = S / 2;
+        constexpr int LG = Log2<H>::v;
+        // a xor b on the left half: f
+#pragma unroll
+        for (int k = 0; k < H; ++k)
+            st.llr[H + k] = minsum_f(parent_llr<N, S>(cx.ych, st, k), parent_llr<N, S>(cx.ych, st, k + H));
+        st.beta[LG] = node<N, LW, FZ, H, OFF>(cx, st);
+        // b on the right half: g with the re-encoded left decisions
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const int a = parent_llr<N, S>(cx.ych, st, k), b = parent_llr<N, S>(cx.ych, st, k + H);
+            st.llr[H + k] = ((st.beta[LG] >> k) & 1ull) ? b - a : b + a;
+        }
+        const uint64_t gr = node<N, LW, FZ, H, OFF + H>(cx, st);
+        const uint64_t be = st.beta[LG];
+        if constexpr (S <= 64) {
+            return (be ^ gr) | (gr << (H & 63));
+        } else {
+            cx.root_cw[0] = be ^ gr;
+            cx.root_cw[1] = gr;
+            return 0;
+        }
+    }
+}
+
+__device__ __forceinline__ int quantize(float y) {
+    int v = __float2int_rn(y * 524288.0f);  // y * 2^19, round to nearest even
+    return max(-kGridMax, min(kGridMax, v));
+}
+
+template <int N, int LW>
+struct SclShape {
+    static constexpr int kFPW = 32 / LW;  // frames per warp
+    static constexpr int kBytesPerWarp = kFPW * N * 4;
+    static constexpr int kWarps = kBytesPerWarp * kWarpsPerBlock <= 32768 ? kWarpsPerBlock
+                                  : (kBytesPerWarp * 2 <= 32768 ? 2 : 1);
+};
+
+template <int N, int LW, class FZ>
+__global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32) scl_kernel(const SclArgs a, const CodeDev c, const FZ fz) {
+    constexpr int FPW = SclShape<N, LW>::kFPW;
+    constexpr int WPB = SclShape<N, LW>::kWarps;
+    constexpr int W = (N + 63) / 64;
+    __shared__ int s_y[WPB][FPW][N];
+    __shared__ unsigned long long s_x[WPB][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = lane / LW, sl = lane % LW;
+    const int64_t fbase = ((int64_t)blockIdx.x * WPB + warp) * FPW;
+    if (fbase >= a.B) return;  // whole warp leaves together
+    for (int idx = lane; idx < FPW * N; idx += 32) {
+        const int64_t f = fbase + idx / N;
+        s_y[warp][idx / N][idx % N] = f < a.B ? quantize(a.y[f * N + (idx % N)]) : 0;
+    }
+    __syncwarp();
+
+    SclCtx<FZ> cx;
+    cx.ych = s_y[warp][seg];
+    cx.xchg = &s_x[warp][seg * LW];
+    cx.lane = sl;
+    cx.count = 1;
+    cx.L = a.L;
+    cx.fz = fz;
+    PathState<N> st;
+    st.pm = 0;
+    uint64_t cw[2];
+    {
+        const uint64_t r = node<N, LW, FZ, N, 0>(cx, st);
+        if constexpr (N <= 64) {
+            cw[0] = r;
+            cw[1] = 0;
+        } else {
+            cw[0] = cx.root_cw[0];
+            cw[1] = cx.root_cw[1];
+        }
+    }
+    const int count = cx.count;
+    const bool valid = sl < count;
+    int pos = sl;
+    if (c.trailing_frozen) {  // frozen leaves after the last branching: stable re-sort by metric
+        int rank = 0;
+#pragma unroll
+        for (int s = 0; s < LW; ++s) {
+            const long long pm_s = __shfl_sync(kFull, st.pm, s, LW);
+            rank += (s < count) && (pm_s < st.pm || (pm_s == st.pm && s < sl));
+        }
+        pos = valid ? rank : sl;
+    }
+    const int64_t frame = fbase + seg;
+    const unsigned segmask = (LW == 32) ? kFull : (((1u << LW) - 1u) << (seg * LW));
+    if (frame >= a.B) return;  // whole segment leaves together
+
+    if (a.mode == 1) {
+        if (valid) {
+            uint64_t *dst = a.list_cw + (frame * a.L + pos) * W;
+            dst[0] = cw[0];
+            if (W > 1) dst[1] = cw[1];
+            a.list_pm[frame * a.L + pos] = st.pm;
+        }
+        return;
+    }
+
+    // CRC in the codeword domain: syndrome bit b = parity(c & mask_b)
+    bool ok = false;
+    if (a.use_crc && valid) {
+        unsigned syn = 0;
+        for (int b = 0; b < c.crc_len; ++b) {
+            const uint64_t *mk = c.crc_masks + (size_t)b * W;
+            int p = __popcll(cw[0] & mk[0]);
+            if (W > 1) p += __popcll(cw[1] & mk[1]);
+            syn |= (unsigned)(p & 1);
+        }
+        ok = syn == 0;
+    }
+    int key = (ok && (a.rule == MPWSD_RULE_ANY || pos == 0)) ? pos : 0x7fff;
+#pragma unroll
+    for (int o = LW / 2; o >= 1; o >>= 1) key = min(key, __shfl_xor_sync(segmask, key, o, LW));
+    if (key != 0x7fff) {
+        if (pos == key) {
+            uint64_t *dst = a.cw_out + frame * W;
+            dst[0] = cw[0];
+            if (W > 1) dst[1] = cw[1];
+            a.flags_out[frame] = (uint16_t)MPWSD_FLAG_CRC_OK;
+        }
+        return;
+    }
+    // stage 2: this frame becomes a slot with one trajectory per list entry
+    int slot = 0, base = 0;
+    if (sl == 0) {
+        slot = atomicAdd(&a.ws.counters[0], 1);
+        base = atomicAdd(&a.ws.counters[1], count);
+    }
+    slot = __shfl_sync(segmask, slot, 0, LW);
+    base = __shfl_sync(segmask, base, 0, LW);
+    if (sl == 0) {
+        int l1 = 0;
+        for (int j = 0; j < N; ++j) l1 += abs(cx.ych[j]);
+        a.ws.slot_frame[slot] = (int)frame;
+        a.ws.slot_l1[slot] = (float)l1 * (1.0f / 524288.0f);
+    }
+    if (sl < a.L) {
+        const int64_t t = (int64_t)slot * a.L + pos;
+        uint64_t *dst = a.ws.traj_cw + t * W;
+        if (valid) {
+            int corr = 0;  // sum_j yhat_j x_j, exact (|.| < 2^30)
+#pragma unroll 8
+            for (int j = 0; j < N; ++j) {
+                const int v = cx.ych[j];
+                corr += ((cw[j >> 6] >> (j & 63)) & 1ull) ? -v : v;
+            }
+            dst[0] = cw[0];
+            if (W > 1) dst[1] = cw[1];
+            a.ws.traj_D[t] = -(double)corr * (1.0 / 524288.0);
+            a.ws.traj_state[t] = kTrajValid;
+            a.ws.act[0][base + pos] = (int)t;
+        } else {
+            dst[0] = 0;
+            if (W > 1) dst[1] = 0;
+            a.ws.traj_D[t] = CUDART_INF;
+            a.ws.traj_state[t] = 0;
+        }
+    }
+}
+
+template <int N, int LW, class FZ>
+cudaError_t launch_one(const CodeDev &c, const SclArgs &a, const FZ &fz, cudaStream_t s) {
+    constexpr int WPB = SclShape<N, LW>::kWarps;
+    constexpr int FPB = WPB * (32 / LW);
+    const int64_t blocks = (a.B + FPB - 1) / FPB;
+    if (blocks == 0) return cudaSuccess;
+    scl_kernel<N, LW, FZ><<<(unsigned)blocks, WPB * 32, 0, s>>>(a, c, fz);
+    return cudaGetLastError();
+}
+
+template <int N, class FZ>
+cudaError_t launch_lw(const CodeDev &c, const SclArgs &a, const FZ &fz, cudaStream_t s) {
+    if (a.L <= 1) return launch_one<N, 1>(c, a, fz, s);
+    if (a.L <= 2) return launch_one<N, 2>(c, a, fz, s);
+    if (a.L <= 4) return launch_one<N, 4>(c, a, fz, s);
+    if (a.L <= 8) return launch_one<N, 8>(c, a, fz, s);
+    if (a.L <= 16) return launch_one<N, 16>(c, a, fz, s);
+    return launch_one<N, 32>(c, a, fz, s);
+}
+
+}  // namespace scl_detail
+
+// Reed-Muller frozen masks, also used by the host to pick a specialisation.
+using scl_detail::rm_mask;
+
+}  // namespace mpwsd

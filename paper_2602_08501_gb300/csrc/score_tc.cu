@@ -1,0 +1,459 @@
+// Scoring step of stage 2 on tcgen05 tensor cores (BF16 hi+lo split).
+//
+// Score of pattern p for a trajectory with centre c (Eq. (5), translation
+// identity of Eq. (3)):   S(p) = sum_{j in supp p} z_j,  z_j = y_j x_j(c).
+// With the 0/1 pattern matrix P (|P| x n) and Z the rows' z vectors this is
+// S = Z P^T, a dense contraction. z is split as z = hi + lo with hi, lo
+// bf16 (|z - hi - lo| <= 2^-16 |z|), so S ~= [Z_hi | Z_lo] [P | P]^T is two
+// bf16 MMAs per K step into one FP32 accumulator; P is exact in bf16. The
+// epilogue keeps the K smallest scores of each row with their indices, so
+// the score matrix never reaches HBM.
+//
+// Kernel shape (sm_103a): persistent, one CTA per SM, 256 threads:
+//   warp 0      bulk-copy producer: 256-pattern tiles of P, stored in HBM as
+//               the exact shared-memory image of a K-major 128B-swizzled
+//               UMMA operand, streamed through a ring of smem stages;
+//   warp 1      TMEM allocator and single-thread MMA issuer
+//               (tcgen05.mma.cta_group::1.kind::f16, M = 128, N = 256, K = 16);
+//   warps 2-3   A builders: gather y and the centre bits of 128 rows, form
+//               z, split to bf16 hi / lo, write the swizzled A tiles;
+//   warps 4-7   epilogue: tcgen05.ld of their 32 TMEM lanes (one row per
+//               thread), running top-K in registers across all pattern tiles.
+// Two TMEM accumulators (2 x 256 columns) let the epilogue of tile j overlap
+// the MMAs of tile j+1. Every mbarrier wait is bounded in time; on expiry the
+// kernel records an error word, drains its own copies, frees TMEM and exits.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace mpwsd {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int kThreads = 256;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: far beyond any legitimate wait
+constexpr unsigned long long kErrTcTimeout = 0x7C01;
+
+template <int N>
+struct TcCfg {
+    static constexpr int KC = N / 64;                   // 64-element (128 B) K chunks
+    static constexpr int A_BUFS = (N == 64) ? 2 : 1;
+    static constexpr int B_STAGES = (N == 64) ? 4 : 2;
+    static constexpr int A_SPLIT_BYTES = BM * N * 2;    // hi or lo part of one A buffer
+    static constexpr int A_BUF_BYTES = 2 * A_SPLIT_BYTES;
+    static constexpr int B_STAGE_BYTES = BN * N * 2;
+    static constexpr int TILE_BYTES = A_BUFS * A_BUF_BYTES + B_STAGES * B_STAGE_BYTES;
+    static constexpr int SMEM_BYTES = TILE_BYTES + 1024 + 256;
+};
+
+// ---- PTX wrappers -------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t tx) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the phase of parity `parity`; false on abort or timeout.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int *abort_flag,
+                                       uint64_t limit_ns) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1; i < (1u << 30); ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 31u) == 0) {
+            if (*abort_flag) return false;
+            if (global_ns() - t0 > limit_ns) return false;
+        }
+    }
+    return false;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major, 128-byte-swizzled operand:
+// start address >> 4 (bits 0-13), leading offset (ignored for this layout),
+// stride 1024 B between 8-row groups (bits 32-45), descriptor version 1
+// (bits 46-47), swizzle mode 128B (bits 61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+#define MPWSD_R8(i) "=r"(v[i + 0]), "=r"(v[i + 1]), "=r"(v[i + 2]), "=r"(v[i + 3]), "=r"(v[i + 4]), "=r"(v[i + 5]), \
+                    "=r"(v[i + 6]), "=r"(v[i + 7])
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : MPWSD_R8(0), MPWSD_R8(8), MPWSD_R8(16), MPWSD_R8(24)
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+#undef MPWSD_R8
+
+__device__ __forceinline__ uint32_t bf16_bits(__nv_bfloat16 h) { return (uint32_t)__bfloat16_as_ushort(h); }
+
+// hi / lo bf16 parts of z (both round to nearest even; z - hi is exact in FP32)
+__device__ __forceinline__ void split_bf16(float z, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(z);
+    const __nv_bfloat16 l = __float2bfloat16_rn(z - __bfloat162float(h));
+    hi = bf16_bits(h);
+    lo = bf16_bits(l);
+}
+
+struct TcShared {
+    uint64_t *b_full, *b_empty, *a_full, *a_empty, *acc_full, *acc_empty;
+    uint32_t *tmem_slot;
+    int *abort_flag;
+};
+
+__device__ __forceinline__ void record_abort(const TcShared &sh, const CodeDev &c) {
+    *(volatile int *)sh.abort_flag = 1;
+    atomicExch(&c.stats->error, kErrTcTimeout);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a, const CodeDev c) {
+    using C = TcCfg<N>;
+    constexpr int W = (N + 63) / 64;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *Abase = smem;
+    uint8_t *Bbase = smem + C::A_BUFS * C::A_BUF_BYTES;
+    uint64_t *bars = (uint64_t *)(Bbase + C::B_STAGES * C::B_STAGE_BYTES);
+    TcShared sh;
+    sh.b_full = bars;
+    sh.b_empty = bars + C::B_STAGES;
+    sh.a_full = bars + 2 * C::B_STAGES;
+    sh.a_empty = sh.a_full + C::A_BUFS;
+    sh.acc_full = sh.a_empty + C::A_BUFS;
+    sh.acc_empty = sh.acc_full + 2;
+    sh.tmem_slot = (uint32_t *)(sh.acc_empty + 2);
+    sh.abort_flag = (int *)(sh.tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nrows = a.n_rows_dev ? *a.n_rows_dev : (int)a.n_rows;
+    const int nblk = (nrows + BM - 1) / BM;
+    const int my_blocks = nblk > (int)blockIdx.x ? (nblk - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    if (my_blocks == 0) return;
+    const int P = (int)c.P;
+    const int nt = (P + BN - 1) / BN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::B_STAGES; ++s) {
+            mbar_init(smem_u32(&sh.b_full[s]), 1);
+            mbar_init(smem_u32(&sh.b_empty[s]), 1);
+        }
+        for (int s = 0; s < C::A_BUFS; ++s) {
+            mbar_init(smem_u32(&sh.a_full[s]), 64);
+            mbar_init(smem_u32(&sh.a_empty[s]), 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&sh.acc_full[s]), 1);
+            mbar_init(smem_u32(&sh.acc_empty[s]), 128);
+        }
+        *sh.abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sh.tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *sh.tmem_slot;
+    const volatile int *abort_flag = sh.abort_flag;
+
+    if (warp == 0) {
+        // ---- producer: pattern tiles into the B ring ----
+        if (lane == 0) {
+            int g = 0;
+            bool ok = true;
+            for (int i = 0; i < my_blocks && ok; ++i) {
+                for (int j = 0; j < nt; ++j, ++g) {
+                    const int s = g % C::B_STAGES;
+                    const uint32_t ph = (uint32_t)(g / C::B_STAGES) & 1u;
+                    if (!mbar_wait(smem_u32(&sh.b_empty[s]), ph ^ 1u, abort_flag, kWaitLimitNs)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t full = smem_u32(&sh.b_full[s]);
+                    mbar_arrive_tx(full, C::B_STAGE_BYTES);
+                    const uint8_t *src = (const uint8_t *)c.pat_tiles + (size_t)j * C::B_STAGE_BYTES;
+                    const uint32_t dst = smem_u32(Bbase + s * C::B_STAGE_BYTES);
+                    for (int part = 0; part < C::B_STAGE_BYTES; part += 16384)
+                        bulk_g2s(dst + part, src + part, 16384, full);
+                }
+            }
+            if (!ok) {
+                record_abort(sh, c);
+                // drain: wait (bounded) for the copies this thread issued
+                const int zero = 0;
+                for (int d = (g > C::B_STAGES ? g - C::B_STAGES : 0); d < g; ++d)
+                    mbar_wait(smem_u32(&sh.b_full[d % C::B_STAGES]), (uint32_t)(d / C::B_STAGES) & 1u,
+                              (const volatile int *)&zero, 10000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            int gb = 0, gacc = 0;
+            bool ok = true;
+            uint32_t last_bar = 0, last_par = 0;
+            for (int i = 0; i < my_blocks && ok; ++i) {
+                const int ab = i % C::A_BUFS;
+                if (!mbar_wait(smem_u32(&sh.a_full[ab]), (uint32_t)(i / C::A_BUFS) & 1u, abort_flag, kWaitLimitNs)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a_hi = smem_u32(Abase + ab * C::A_BUF_BYTES);
+                const uint32_t a_lo = a_hi + C::A_SPLIT_BYTES;
+                for (int j = 0; j < nt; ++j, ++gb, ++gacc) {
+                    const int s = gb % C::B_STAGES;
+                    if (!mbar_wait(smem_u32(&sh.b_full[s]), (uint32_t)(gb / C::B_STAGES) & 1u, abort_flag,
+                                   kWaitLimitNs)) {
+                        ok = false;
+                        break;
+                    }
+                    const int acc = gacc & 1;
+                    if (!mbar_wait(smem_u32(&sh.acc_empty[acc]), ((uint32_t)(gacc >> 1) & 1u) ^ 1u, abort_flag,
+                                   kWaitLimitNs)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t bsm = smem_u32(Bbase + s * C::B_STAGE_BYTES);
+                    const uint32_t d = tmem + (uint32_t)(acc * BN);
+                    uint32_t accum = 0;
+#pragma unroll
+                    for (int split = 0; split < 2; ++split) {
+                        const uint32_t asm_base = split ? a_lo : a_hi;
+#pragma unroll
+                        for (int kc = 0; kc < C::KC; ++kc) {
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t ad = sw128_desc(asm_base + kc * (BM * 128) + kk * 32);
+                                const uint64_t bd = sw128_desc(bsm + kc * (BN * 128) + kk * 32);
+                                mma_bf16(d, ad, bd, idesc, accum);
+                                accum = 1;
+                            }
+                        }
+                    }
+                    mma_commit(smem_u32(&sh.b_empty[s]));
+                    mma_commit(smem_u32(&sh.acc_full[acc]));
+                    last_bar = smem_u32(&sh.acc_full[acc]);
+                    last_par = (uint32_t)(gacc >> 1) & 1u;
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&sh.a_empty[ab]));
+            }
+            if (!ok) {
+                record_abort(sh, c);
+                // drain: the last committed MMAs must finish before TMEM is freed
+                if (last_bar) {
+                    const int zero = 0;
+                    mbar_wait(last_bar, last_par, (const volatile int *)&zero, 10000000ull);
+                }
+            }
+        }
+    } else if (warp < 4) {
+        // ---- A builders: z = y (.) x(c) split into bf16 hi / lo, swizzled ----
+        const int aw = warp - 2;  // 0 or 1: even / odd rows
+        for (int i = 0; i < my_blocks; ++i) {
+            const int ab = i % C::A_BUFS;
+            bool ok = mbar_wait(smem_u32(&sh.a_empty[ab]), ((uint32_t)(i / C::A_BUFS) & 1u) ^ 1u, abort_flag,
+                                kWaitLimitNs);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) record_abort(sh, c);
+                break;
+            }
+            const int rb = (int)blockIdx.x + i * (int)gridDim.x;
+            uint8_t *Ahi = Abase + ab * C::A_BUF_BYTES;
+            uint8_t *Alo = Ahi + C::A_SPLIT_BYTES;
+            for (int r = aw; r < BM; r += 2) {
+                const int row = rb * BM + r;
+                uint32_t hi[N / 32], lo[N / 32];  // N/32 elements per lane
+                if (row < nrows) {
+                    const int t = a.rows ? a.rows[row] : row;
+                    const int frame = a.row_frame ? a.row_frame[row] : a.slot_frame[t / a.L];
+                    const float *yr = a.y + (int64_t)frame * N;
+                    const uint64_t *cw = a.cw + (int64_t)t * W;
+#pragma unroll
+                    for (int e = 0; e < N / 32; ++e) {
+                        const int j = lane * (N / 32) + e;
+                        const float v = grid_f(yr[j]);
+                        const float z = ((cw[j >> 6] >> (j & 63)) & 1ull) ? -v : v;
+                        split_bf16(z, hi[e], lo[e]);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < N / 32; ++e) hi[e] = lo[e] = 0;
+                }
+                // element j of row r: chunk j/64, 16-B unit (j%64)/8 stored at unit ^ (r%8)
+                const int j0 = lane * (N / 32);
+                const int kc = j0 / 64, e64 = j0 % 64;
+                const int unit = e64 / 8, within = (e64 % 8) * 2;
+                const int off = kc * (BM * 128) + (r / 8) * 1024 + (r % 8) * 128 + ((unit ^ (r % 8)) * 16) + within;
+                if constexpr (N == 64) {
+                    *(uint32_t *)(Ahi + off) = hi[0] | (hi[1] << 16);
+                    *(uint32_t *)(Alo + off) = lo[0] | (lo[1] << 16);
+                } else {
+                    *(uint2 *)(Ahi + off) = make_uint2(hi[0] | (hi[1] << 16), hi[2] | (hi[3] << 16));
+                    *(uint2 *)(Alo + off) = make_uint2(lo[0] | (lo[1] << 16), lo[2] | (lo[3] << 16));
+                }
+            }
+            fence_proxy_async();
+            mbar_arrive(smem_u32(&sh.a_full[ab]));
+        }
+    } else {
+        // ---- epilogue: TMEM -> registers -> running top-K per row ----
+        const int q = warp & 3;              // TMEM lane quadrant
+        const int r = q * 32 + lane;         // row within the block
+        int gacc = 0;
+        bool ok = true;
+        for (int i = 0; i < my_blocks && ok; ++i) {
+            const int rb = (int)blockIdx.x + i * (int)gridDim.x;
+            float tv[kTopK];
+            int ti[kTopK];
+#pragma unroll
+            for (int k = 0; k < kTopK; ++k) {
+                tv[k] = CUDART_INF_F;
+                ti[k] = -1;
+            }
+            for (int j = 0; j < nt; ++j, ++gacc) {
+                const int acc = gacc & 1;
+                bool w = mbar_wait(smem_u32(&sh.acc_full[acc]), (uint32_t)(gacc >> 1) & 1u, abort_flag, kWaitLimitNs);
+                w = __all_sync(0xffffffffu, w);
+                if (!w) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const int col0 = j * BN;
+#pragma unroll 1
+                for (int ch = 0; ch < BN / 32; ++ch) {
+                    uint32_t v[32];
+                    __syncwarp();
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + ch * 32), v);
+                    const int cbase = col0 + ch * 32;
+                    float mn = CUDART_INF_F;
+                    const bool full = cbase + 32 <= P;
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const float s = __uint_as_float(v[e]);
+                        mn = (full || cbase + e < P) ? fminf(mn, s) : mn;
+                    }
+                    if (mn < tv[kTopK - 1]) {
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const float s = __uint_as_float(v[e]);
+                            if ((full || cbase + e < P) && s < tv[kTopK - 1]) topk_insert<kTopK>(tv, ti, s, cbase + e);
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(smem_u32(&sh.acc_empty[acc]));
+            }
+            if (!ok) break;
+            const int row = rb * BM + r;
+            if (row < nrows) {
+#pragma unroll
+                for (int k = 0; k < kTopK; ++k) {
+                    a.topk_val[(int64_t)row * kTopK + k] = tv[k];
+                    a.topk_idx[(int64_t)row * kTopK + k] = ti[k];
+                }
+            }
+        }
+        if (!ok && lane == 0) record_abort(sh, c);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+template <int N>
+cudaError_t launch_n(const CodeDev &c, const ScoreArgs &a, cudaStream_t s) {
+    constexpr int smem = TcCfg<N>::SMEM_BYTES;
+    cudaError_t e = cudaFuncSetAttribute(score_tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int64_t grid = c.num_sms;
+    if (!a.n_rows_dev) grid = std::min<int64_t>(grid, (a.n_rows + BM - 1) / BM);
+    if (grid <= 0) return cudaSuccess;
+    score_tc_kernel<N><<<(unsigned)grid, kThreads, smem, s>>>(a, c);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool score_tc_supported(const CodeDev &c) { return (c.n == 64 || c.n == 128) && c.pat_tiles != nullptr; }
+
+cudaError_t launch_score_tc(const CodeDev &c, const ScoreArgs &a, cudaStream_t s) {
+    if (c.n == 64) return launch_n<64>(c, a, s);
+    if (c.n == 128) return launch_n<128>(c, a, s);
+    return cudaErrorNotSupported;
+}
+
+}  // namespace mpwsd

@@ -193,3 +193,16 @@ def test_golden_regression(oracle_mod):
     out = code.decode(wl.y, gold["L"], gold["T"], threads=2)
     assert [f"{int(w):016x}" for w in out["cw"][:, 0]] == gold["cw_hex"]
     assert out["flags"].tolist() == gold["flags"]
+
+
+def test_gains_match_ed_differences(oracle_mod):
+    """G(p) of Eq. (5) equals (ED(c) - ED(c xor p)) / 2 for squared ED."""
+    code = oracle_mod.rm_code(6, 2)
+    pats = code.enumerate_codewords([16])
+    code = code.with_patterns(pats)
+    P = oracle_mod.unpack_bits(pats, 64)
+    ys, cs = _frames(code, 5, 1.2, seed=12)
+    for y, c in zip(ys, cs):
+        G = code.gains(y, c)
+        for p in (0, 7, 100, 2603):
+            assert G[p] == (_ed(y, c) - _ed(y, c ^ P[p])) / 2
