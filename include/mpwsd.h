@@ -218,6 +218,28 @@ MPWSD_API int mpwsd_score_topk(mpwsd_code *code, int score_mode, const float *y_
  * by earlier work of this handle: MPWSD_OK or MPWSD_ETIMEOUT. */
 MPWSD_API int mpwsd_sync(mpwsd_code *code, void *stream);
 
+/* Kernel classes for mpwsd_profile_end. */
+#define MPWSD_KERNEL_SCL 0        /* stage 1: SC-list + CRC + compaction */
+#define MPWSD_KERNEL_SCORE_TC 1   /* scoring, tcgen05 BF16 hi+lo */
+#define MPWSD_KERNEL_SCORE_FP32 2 /* scoring, FP32 CUDA cores */
+#define MPWSD_KERNEL_HOP 3        /* FP64 near-tie re-rank + hop + compaction */
+#define MPWSD_KERNEL_RESCAN 4     /* full FP64 rescan of overflowing rows */
+#define MPWSD_KERNEL_FINAL 5      /* per-frame argmin ED + flags */
+#define MPWSD_KERNEL_KINDS 6
+
+typedef struct mpwsd_kernel_time {
+    int64_t launches; /* kernels of this class launched while profiling */
+    double ms;        /* summed device time between CUDA events recorded around each launch */
+} mpwsd_kernel_time;
+
+/* mpwsd_profile_begin: from now on, record a CUDA event pair on the launch
+ * stream around every kernel this handle launches (a few microseconds of
+ * overhead per launch). mpwsd_profile_end: wait for those events, write the
+ * per-class launch counts and summed durations to out[MPWSD_KERNEL_KINDS],
+ * and stop recording. */
+MPWSD_API int mpwsd_profile_begin(mpwsd_code *code);
+MPWSD_API int mpwsd_profile_end(mpwsd_code *code, mpwsd_kernel_time *out);
+
 /* Read (synchronising the device) / reset the handle's counters. */
 MPWSD_API int mpwsd_stats_get(mpwsd_code *code, mpwsd_stats *out);
 MPWSD_API int mpwsd_stats_reset(mpwsd_code *code);

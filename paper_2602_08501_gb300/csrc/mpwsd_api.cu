@@ -76,7 +76,46 @@ struct mpwsd_code {
     mpwsd_workspace *default_ws = nullptr;
     std::atomic<long long> launches{0};
     std::mutex mu;
+    // kernel timing (mpwsd_profile_begin / end)
+    bool profiling = false;
+    std::mutex prof_mu;
+    struct Rec {
+        int kind;
+        cudaEvent_t start, stop;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
 };
+
+namespace {
+
+cudaEvent_t pool_event(mpwsd_code *c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch through `fn`, counting it and, while profiling, bracketing it with
+// CUDA events on the launch stream.
+template <class Fn>
+cudaError_t timed_launch(mpwsd_code *c, int kind, cudaStream_t s, Fn &&fn) {
+    c->launches++;
+    if (!c->profiling) return fn();
+    std::lock_guard<std::mutex> lk(c->prof_mu);
+    cudaEvent_t a = pool_event(c), b = pool_event(c);
+    cudaEventRecord(a, s);
+    cudaError_t e = fn();
+    cudaEventRecord(b, s);
+    c->recs.push_back({kind, a, b});
+    return e;
+}
+
+}  // namespace
 
 extern "C" const char *mpwsd_strerror(int status) {
     switch (status) {
@@ -376,6 +415,11 @@ extern "C" void mpwsd_workspace_free(mpwsd_workspace *ws) {
 extern "C" void mpwsd_free_code(mpwsd_code *code) {
     if (!code) return;
     cudaDeviceSynchronize();
+    for (auto &r : code->recs) {
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.stop);
+    }
+    for (auto e : code->pool) cudaEventDestroy(e);
     mpwsd_workspace_free(code->default_ws);
     free_code_device(code->d);
     delete code;
@@ -405,9 +449,9 @@ static int check_device(const mpwsd_code *code) {
 }
 
 static cudaError_t launch_score(mpwsd_code *code, int mode, const ScoreArgs &a, cudaStream_t s) {
-    code->launches++;
-    if (mode == MPWSD_SCORE_FP32) return launch_score_fp32(code->d, a, s);
-    return launch_score_tc(code->d, a, s);
+    if (mode == MPWSD_SCORE_FP32)
+        return timed_launch(code, MPWSD_KERNEL_SCORE_FP32, s, [&] { return launch_score_fp32(code->d, a, s); });
+    return timed_launch(code, MPWSD_KERNEL_SCORE_TC, s, [&] { return launch_score_tc(code->d, a, s); });
 }
 
 static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int64_t B, int L, int T,
@@ -425,8 +469,7 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
     sa.cw_out = cw_dev;
     sa.flags_out = flags_dev;
     sa.ws = ws;
-    code->launches++;
-    e = launch_scl(d, sa, s);
+    e = timed_launch(code, MPWSD_KERNEL_SCL, s, [&] { return launch_scl(d, sa, s); });
     if (e != cudaSuccess) return cuda_fail(e, "stage-1 launch");
     for (int it = 0; it < T; ++it) {
         ScoreArgs a{};
@@ -440,13 +483,12 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
         a.topk_idx = ws.topk_idx;
         e = launch_score(code, o.score_mode, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "scoring launch");
-        code->launches += 2;
-        e = launch_hop(d, ws, it, L, y_dev, s);
-        if (e == cudaSuccess) e = launch_rescan(d, ws, it, L, y_dev, s);
+        e = timed_launch(code, MPWSD_KERNEL_HOP, s, [&] { return launch_hop(d, ws, it, L, y_dev, s); });
+        if (e == cudaSuccess)
+            e = timed_launch(code, MPWSD_KERNEL_RESCAN, s, [&] { return launch_rescan(d, ws, it, L, y_dev, s); });
         if (e != cudaSuccess) return cuda_fail(e, "hop launch");
     }
-    code->launches++;
-    e = launch_final(d, ws, L, T, B, cw_dev, flags_dev, s);
+    e = timed_launch(code, MPWSD_KERNEL_FINAL, s, [&] { return launch_final(d, ws, L, T, B, cw_dev, flags_dev, s); });
     if (e != cudaSuccess) return cuda_fail(e, "final launch");
     return MPWSD_OK;
 }
@@ -512,8 +554,8 @@ extern "C" int mpwsd_stage1_list(mpwsd_code *code, const float *y_dev, int64_t B
     sa.mode = 1;
     sa.list_cw = list_cw_dev;
     sa.list_pm = list_pm_dev;
-    code->launches++;
-    cudaError_t e = launch_scl(code->d, sa, (cudaStream_t)stream);
+    cudaError_t e = timed_launch(code, MPWSD_KERNEL_SCL, (cudaStream_t)stream,
+                                 [&] { return launch_scl(code->d, sa, (cudaStream_t)stream); });
     if (e != cudaSuccess) return cuda_fail(e, "stage-1 launch");
     return MPWSD_OK;
 }
@@ -574,6 +616,41 @@ extern "C" int mpwsd_stats_get(mpwsd_code *code, mpwsd_stats *out) {
     out->hops = (int64_t)ds.hops;
     out->kernel_launches = code->launches.load();
     return MPWSD_OK;
+}
+
+extern "C" int mpwsd_profile_begin(mpwsd_code *code) {
+    if (!code) return fail(MPWSD_EINVAL, "code is NULL");
+    std::lock_guard<std::mutex> lk(code->prof_mu);
+    for (auto &r : code->recs) {
+        code->pool.push_back(r.start);
+        code->pool.push_back(r.stop);
+    }
+    code->recs.clear();
+    code->profiling = true;
+    return MPWSD_OK;
+}
+
+extern "C" int mpwsd_profile_end(mpwsd_code *code, mpwsd_kernel_time *out) {
+    if (!code || !out) return fail(MPWSD_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(code->prof_mu);
+    code->profiling = false;
+    for (int k = 0; k < MPWSD_KERNEL_KINDS; ++k) {
+        out[k].launches = 0;
+        out[k].ms = 0.0;
+    }
+    int status = MPWSD_OK;
+    for (auto &r : code->recs) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(r.stop);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.start, r.stop);
+        if (e != cudaSuccess && status == MPWSD_OK) status = cuda_fail(e, "reading kernel timers");
+        out[r.kind].launches += 1;
+        out[r.kind].ms += ms;
+        code->pool.push_back(r.start);
+        code->pool.push_back(r.stop);
+    }
+    code->recs.clear();
+    return status;
 }
 
 extern "C" int mpwsd_stats_reset(mpwsd_code *code) {

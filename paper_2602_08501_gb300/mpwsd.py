@@ -40,6 +40,13 @@ class _Opts(ctypes.Structure):
                 ("reserved", ctypes.c_int * 5)]
 
 
+class _KTime(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
+KERNEL_NAMES = ("scl", "score_tc", "score_fp32", "hop", "rescan", "final")
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("frames", "stage2_frames", "trajectories", "pattern_evals",
                                                "rerank_candidates", "rescans", "hops", "kernel_launches")]
@@ -79,6 +86,8 @@ def lib():
             "mpwsd_stats_get": (i32, [P, ctypes.POINTER(_Stats)]),
             "mpwsd_stats_reset": (i32, [P]),
             "mpwsd_enumerate_codewords": (i32, [i32, P, P, i32, P, i64, ctypes.POINTER(ctypes.c_int64)]),
+            "mpwsd_profile_begin": (i32, [P]),
+            "mpwsd_profile_end": (i32, [P, ctypes.POINTER(_KTime)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -263,3 +272,13 @@ class Code:
 
     def reset_stats(self):
         _check(lib().mpwsd_stats_reset(self._h), "stats_reset")
+
+    def profile_begin(self):
+        """Record CUDA events around every kernel this handle launches."""
+        _check(lib().mpwsd_profile_begin(self._h), "profile_begin")
+
+    def profile_end(self) -> dict:
+        """Per kernel class: {"launches": n, "ms": summed device time}."""
+        arr = (_KTime * len(KERNEL_NAMES))()
+        _check(lib().mpwsd_profile_end(self._h, arr), "profile_end")
+        return {name: {"launches": int(arr[i].launches), "ms": float(arr[i].ms)} for i, name in enumerate(KERNEL_NAMES)}
