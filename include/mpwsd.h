@@ -187,6 +187,34 @@ MPWSD_API int mpwsd_decode_ws(mpwsd_code *code, mpwsd_workspace *ws, const float
                     const mpwsd_opts *opts, uint64_t *cw_dev, uint16_t *flags_dev, void *stream);
 
 /*
+ * mpwsd_decode_noalloc -- mpwsd_decode for callers that cannot allocate device
+ * memory when they decode. The paper has no counterpart: this is an interface
+ * of the library. Typical such callers record their work into a CUDA graph
+ * (cudaMalloc is not allowed while a stream is being captured), run serving
+ * threads that must not call an allocator once warmed up, or live in a host
+ * whose device memory belongs to an allocator the library must not bypass.
+ *
+ * Same arguments and results as mpwsd_decode; the caller still provides y_dev,
+ * cw_dev and flags_dev. The scratch is one fixed 4 MiB array in device memory
+ * that every GPU loading the library keeps until the process exits; this
+ * entry point never calls cudaMalloc, cudaFree or any allocating routine.
+ *  - Capacity: B frames with list size L must fit in 4 MiB of scratch (about
+ *    50,000 to 60,000 trajectories B*L); larger requests return MPWSD_EINVAL
+ *    with the sizes in mpwsd_last_error().
+ *  - Set-up: the first call on each device (with that device current) looks
+ *    up the array's device address; make that first call before any stream
+ *    capture begins.
+ *  - Sharing: every call on a device uses the same array and finds the
+ *    previous call's contents in it (the counters it needs zeroed are cleared
+ *    on the stream). Calls whose work overlaps on the GPU, on any stream or
+ *    code handle, race on the array: serialise them.
+ *  - MPWSD_EINVAL while mpwsd_profile_begin is active on the handle (kernel
+ *    timing creates CUDA events).
+ */
+MPWSD_API int mpwsd_decode_noalloc(mpwsd_code *code, const float *y_dev, int64_t B, int L, int T,
+                                   const mpwsd_opts *opts, uint64_t *cw_dev, uint16_t *flags_dev, void *stream);
+
+/*
  * mpwsd_stage1_list -- stage 1 alone (Sec. III-A): min-sum SC-list decoding
  * of B frames, returning the whole final list in order (best metric first).
  *

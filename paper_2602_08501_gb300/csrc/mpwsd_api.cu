@@ -716,3 +716,71 @@ extern "C" int mpwsd_enumerate_codewords(int n, const uint8_t *frozen, const int
     }
     return MPWSD_OK;
 }
+
+// ---- allocation-free decode ---------------------------------------------------
+//
+// Some callers cannot allocate device memory at decode time: code running
+// while a CUDA stream is being captured into a graph (cudaMalloc is not
+// allowed there), serving threads that must not touch the allocator once
+// warmed up, and hosts whose device memory is owned by another allocator that
+// the library must not bypass. For them, mpwsd_decode_noalloc runs the same
+// decode with its scratch in one file-scope device array of fixed size.
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)4 << 20;  // 4 MiB per device, held until process exit
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array for the current device, looked up once
+// per device (with that device current). In host code the array's name is
+// only a host-side handle, never a device address.
+int noalloc_scratch(void **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(MPWSD_EUNSUPPORTED, "device %d beyond %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress of the scratch array");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return MPWSD_OK;
+}
+
+}  // namespace
+
+extern "C" int mpwsd_decode_noalloc(mpwsd_code *code, const float *y_dev, int64_t B, int L, int T,
+                                    const mpwsd_opts *opts, uint64_t *cw_dev, uint16_t *flags_dev, void *stream) {
+    mpwsd_opts o;
+    int st = check_decode_args(code, y_dev, B, L, T, opts, cw_dev, flags_dev, &o);
+    if (st) return st;
+    if (code->profiling)
+        return fail(MPWSD_EINVAL, "kernel timing is on for this handle (it creates CUDA events); "
+                                  "call mpwsd_profile_end first");
+    const size_t need = ws_layout(code->d, std::max<int64_t>(B, 1), L, nullptr);
+    if (need > kNoAllocScratchBytes)
+        return fail(MPWSD_EINVAL,
+                    "B = %lld frames with L = %d need %zu bytes of scratch; the allocation-free entry point has %zu "
+                    "(about %lld trajectories B*L for n = %d)",
+                    (long long)B, L, need, kNoAllocScratchBytes,
+                    (long long)(kNoAllocScratchBytes / (need / std::max<int64_t>((int64_t)B * L, 1))), code->d.n);
+    if (B == 0) return MPWSD_OK;
+    void *base = nullptr;
+    st = noalloc_scratch(&base);
+    if (st) return st;
+    Workspace ws;
+    ws.base = base;
+    ws.bytes = need;
+    ws.max_B = B;
+    ws.max_L = L;
+    cudaGetDevice(&ws.device);
+    ws_layout(code->d, B, L, &ws);
+    return decode_impl(code, ws, y_dev, B, L, T, o, cw_dev, flags_dev, (cudaStream_t)stream);
+}
