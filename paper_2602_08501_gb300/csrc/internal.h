@@ -9,6 +9,7 @@
 namespace mpwsd {
 
 constexpr int kTopK = MPWSD_TOPK;
+constexpr int kTcPatternsPerTile = 128;  // pattern tile of the tensor-core scoring kernel
 constexpr int kGridShift = 19;            // y is read on the 2^-19 grid
 constexpr int kGridMax = (1 << 23) - 1;   // |round(y 2^19)| <= 2^23 - 1
 // Margin of the near-tie re-rank: every approximate score is within
@@ -67,7 +68,7 @@ struct CodeDev {
     // device arrays
     uint64_t *pat_bits = nullptr;   // P x W
     uint32_t *pat_supp = nullptr;   // P x wq_max, 4 uint8 indices per word, padded with index n
-    uint16_t *pat_tiles = nullptr;  // ceil(P/256) tiles of 256 x n bf16, smem image (128B swizzle, K-major)
+    uint16_t *pat_tiles = nullptr;  // ceil(P/128) tiles of 128 x n bf16, smem image (128B swizzle, K-major)
     int64_t n_tiles = 0;
     uint64_t *crc_masks = nullptr;  // crc_len x W, codeword domain: syndrome bit b = parity(c & mask_b)
     DevStats *stats = nullptr;

@@ -249,25 +249,26 @@ extern "C" int mpwsd_load_code(int n, const uint8_t *G, const uint8_t *frozen, i
             supp[(size_t)p * d.wq_max + q] = (uint32_t)idx[4 * q] | ((uint32_t)idx[4 * q + 1] << 8) |
                                              ((uint32_t)idx[4 * q + 2] << 16) | ((uint32_t)idx[4 * q + 3] << 24);
     }
-    // bf16 0/1 pattern tiles, 256 patterns x n per tile, laid out as the shared
-    // memory image a K-major 128-byte-swizzled UMMA operand expects: for each
-    // 64-element K chunk, rows of 128 B grouped in 1024-B atoms, 16-B unit u of
-    // row r stored at unit u ^ (r % 8).
-    d.n_tiles = (n_patterns + 255) / 256;
+    // bf16 0/1 pattern tiles, kTcPatternsPerTile patterns x n per tile, laid
+    // out as the shared memory image a K-major 128-byte-swizzled UMMA operand
+    // expects: for each 64-element K chunk, rows of 128 B grouped in 1024-B
+    // atoms, 16-B unit u of row r stored at unit u ^ (r % 8).
+    constexpr int TP = kTcPatternsPerTile;
+    d.n_tiles = (n_patterns + TP - 1) / TP;
     const int kchunks = n / 64 > 0 ? n / 64 : 1;
-    const size_t tile_elems = (size_t)256 * kchunks * 64;
+    const size_t tile_elems = (size_t)TP * kchunks * 64;
     std::vector<uint16_t> tiles;
     if (n >= 64) {
         tiles.assign((size_t)d.n_tiles * tile_elems, 0);
         const uint16_t one = f32_to_bf16_bits(1.0f);
         for (int64_t p = 0; p < n_patterns; ++p) {
-            const int64_t tile = p / 256;
-            const int r = (int)(p % 256);
+            const int64_t tile = p / TP;
+            const int r = (int)(p % TP);
             for (int j = 0; j < n; ++j) {
                 if (!((patterns[p * W + j / 64] >> (j % 64)) & 1ull)) continue;
                 const int kc = j / 64, e64 = j % 64;
                 const int unit = e64 / 8, within = e64 % 8;
-                const size_t off = (size_t)tile * tile_elems + (size_t)kc * 256 * 64 + (size_t)r * 64 +
+                const size_t off = (size_t)tile * tile_elems + (size_t)kc * TP * 64 + (size_t)r * 64 +
                                    (size_t)((unit ^ (r % 8)) * 8 + within);
                 tiles[off] = one;
             }

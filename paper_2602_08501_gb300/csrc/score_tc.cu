@@ -9,16 +9,22 @@
 // epilogue keeps the K smallest scores of each row with their indices, so
 // the score matrix never reaches HBM.
 //
-// Kernel shape (sm_103a): persistent, one CTA per SM, 256 threads:
-//   warp 0      bulk-copy producer: 256-pattern tiles of P, stored in HBM as
+// Kernel shape (sm_103a): persistent, one CTA per SM, 384 threads, units of
+// 256 rows (two 128-row blocks that share every pattern tile, halving the L2
+// traffic of the pattern stream per flop):
+//   warp 0      bulk-copy producer: 128-pattern tiles of P, stored in HBM as
 //               the exact shared-memory image of a K-major 128B-swizzled
 //               UMMA operand, streamed through a ring of smem stages;
 //   warp 1      TMEM allocator and single-thread MMA issuer
-//               (tcgen05.mma.cta_group::1.kind::f16, M = 128, N = 256, K = 16);
-//   warps 2-3   A builders: gather y and the centre bits of 128 rows, form
-//               z, split to bf16 hi / lo, write the swizzled A tiles;
-//   warps 4-7   epilogue: tcgen05.ld of their 32 TMEM lanes (one row per
-//               thread), running top-K in registers across all pattern tiles.
+//               (tcgen05.mma.cta_group::1.kind::f16, M = 128, N = 128, K = 16,
+//               two MMAs per K step, one per row block);
+//   warps 2-3   A builders (one per row block): gather frame and centre of
+//               4 rows per lane, then y rows 16 at a time, form z, split to
+//               bf16 hi / lo, write the swizzled A tiles;
+//   warps 4-11  epilogue (row block (warp-4)/4, TMEM lane quadrant warp%4):
+//               tcgen05.ld x64 of 32 TMEM lanes (one row per thread), minima
+//               of 8-column groups with three-input mins, and only groups
+//               that beat the row's 4th best enter the running top-K.
 // Two TMEM accumulators (2 x 256 columns) let the epilogue of tile j overlap
 // the MMAs of tile j+1. Every mbarrier wait is bounded in time; on expiry the
 // kernel records an error word, drains its own copies, frees TMEM and exits.
@@ -31,22 +37,26 @@
 namespace mpwsd {
 namespace {
 
-constexpr int BM = 128;
-constexpr int BN = 256;
-constexpr int kThreads = 256;
+constexpr int BM = 128;                 // rows per MMA (TMEM lanes)
+constexpr int RB = 2;                   // row blocks per unit, sharing every pattern tile
+constexpr int UM = BM * RB;             // rows per unit
+constexpr int BN = kTcPatternsPerTile;  // patterns per tile (MMA N)
+constexpr int kThreads = 384;                // 12 warps: producer, MMA, 2 builders, 8 epilogue
+constexpr int kEpiThreads = 256;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: far beyond any legitimate wait
 constexpr unsigned long long kErrTcTimeout = 0x7C01;
 
 template <int N>
 struct TcCfg {
-    static constexpr int KC = N / 64;                   // 64-element (128 B) K chunks
+    static constexpr int KC = N / 64;                    // 64-element (128 B) K chunks
     static constexpr int A_BUFS = (N == 64) ? 2 : 1;
-    static constexpr int B_STAGES = (N == 64) ? 4 : 2;
-    static constexpr int A_SPLIT_BYTES = BM * N * 2;    // hi or lo part of one A buffer
-    static constexpr int A_BUF_BYTES = 2 * A_SPLIT_BYTES;
+    static constexpr int B_STAGES = (N == 64) ? 4 : 3;
+    static constexpr int A_PART_BYTES = BM * N * 2;      // one row block, hi or lo
+    static constexpr int A_BUF_BYTES = RB * 2 * A_PART_BYTES;
     static constexpr int B_STAGE_BYTES = BN * N * 2;
     static constexpr int TILE_BYTES = A_BUFS * A_BUF_BYTES + B_STAGES * B_STAGE_BYTES;
     static constexpr int SMEM_BYTES = TILE_BYTES + 1024 + 256;
+    static constexpr int G = (N == 64) ? 16 : 8;         // rows whose y loads are in flight together
 };
 
 // ---- PTX wrappers -------------------------------------------------------------
@@ -131,18 +141,71 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+
 #define MPWSD_R8(i) "=r"(v[i + 0]), "=r"(v[i + 1]), "=r"(v[i + 2]), "=r"(v[i + 3]), "=r"(v[i + 4]), "=r"(v[i + 5]), \
                     "=r"(v[i + 6]), "=r"(v[i + 7])
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+// 64 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : MPWSD_R8(0), MPWSD_R8(8), MPWSD_R8(16), MPWSD_R8(24)
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        : MPWSD_R8(0), MPWSD_R8(8), MPWSD_R8(16), MPWSD_R8(24), MPWSD_R8(32), MPWSD_R8(40), MPWSD_R8(48),
+          MPWSD_R8(56)
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 #undef MPWSD_R8
+
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// minimum of the 8 values v[8g .. 8g+7]
+template <int G8>
+__device__ __forceinline__ float min8(const uint32_t (&v)[64]) {
+    return fmin3(fmin3(__uint_as_float(v[8 * G8]), __uint_as_float(v[8 * G8 + 1]), __uint_as_float(v[8 * G8 + 2])),
+                 fmin3(__uint_as_float(v[8 * G8 + 3]), __uint_as_float(v[8 * G8 + 4]), __uint_as_float(v[8 * G8 + 5])),
+                 fminf(__uint_as_float(v[8 * G8 + 6]), __uint_as_float(v[8 * G8 + 7])));
+}
+
+// Move every value of group G8 that beats the row's current K-th best into
+// the running top-K: take the group minimum, insert it (its lowest position on
+// ties), blank it, repeat. Usually zero or one round.
+template <int G8>
+__device__ __forceinline__ void drain_group(uint32_t (&v)[64], float gm, float (&tv)[kTopK], int (&ti)[kTopK],
+                                            int cbase) {
+    while (gm < tv[kTopK - 1]) {
+        int pos = 7;
+#pragma unroll
+        for (int e = 6; e >= 0; --e) pos = (__uint_as_float(v[8 * G8 + e]) == gm) ? e : pos;
+        topk_insert<kTopK>(tv, ti, gm, cbase + 8 * G8 + pos);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[8 * G8 + e] = (e == pos) ? __float_as_uint(CUDART_INF_F) : v[8 * G8 + e];
+        gm = min8<G8>(v);
+    }
+}
+
+template <int G8>
+__device__ __forceinline__ void scan_groups(uint32_t (&v)[64], const float (&gm)[8], float (&tv)[kTopK],
+                                            int (&ti)[kTopK], int cbase) {
+    if constexpr (G8 < 8) {
+        if (gm[G8] < tv[kTopK - 1]) drain_group<G8>(v, gm[G8], tv, ti, cbase);
+        scan_groups<G8 + 1>(v, gm, tv, ti, cbase);
+    }
+}
+
+template <int G8>
+__device__ __forceinline__ void group_mins(const uint32_t (&v)[64], float (&gm)[8]) {
+    if constexpr (G8 < 8) {
+        gm[G8] = min8<G8>(v);
+        group_mins<G8 + 1>(v, gm);
+    }
+}
 
 __device__ __forceinline__ uint32_t bf16_bits(__nv_bfloat16 h) { return (uint32_t)__bfloat16_as_ushort(h); }
 
@@ -169,6 +232,7 @@ template <int N>
 __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a, const CodeDev c) {
     using C = TcCfg<N>;
     constexpr int W = (N + 63) / 64;
+    constexpr int EPL = N / 32;  // elements of a row per lane in the A builder
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *Abase = smem;
@@ -186,9 +250,10 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nrows = a.n_rows_dev ? *a.n_rows_dev : (int)a.n_rows;
-    const int nblk = (nrows + BM - 1) / BM;
-    const int my_blocks = nblk > (int)blockIdx.x ? (nblk - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
-    if (my_blocks == 0) return;
+    const int nunits = (nrows + UM - 1) / UM;
+    const int my_units =
+        nunits > (int)blockIdx.x ? (nunits - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    if (my_units == 0) return;
     const int P = (int)c.P;
     const int nt = (P + BN - 1) / BN;
 
@@ -203,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(smem_u32(&sh.acc_full[s]), 1);
-            mbar_init(smem_u32(&sh.acc_empty[s]), 128);
+            mbar_init(smem_u32(&sh.acc_empty[s]), kEpiThreads);
         }
         *sh.abort_flag = 0;
         fence_mbar_init();
@@ -225,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
         if (lane == 0) {
             int g = 0;
             bool ok = true;
-            for (int i = 0; i < my_blocks && ok; ++i) {
+            for (int i = 0; i < my_units && ok; ++i) {
                 for (int j = 0; j < nt; ++j, ++g) {
                     const int s = g % C::B_STAGES;
                     const uint32_t ph = (uint32_t)(g / C::B_STAGES) & 1u;
@@ -251,21 +316,20 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
             }
         }
     } else if (warp == 1) {
-        // ---- MMA issuer ----
+        // ---- MMA issuer: per tile and K step, one 128 x BN x 16 MMA per row block ----
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16(BM, BN);
             int gb = 0, gacc = 0;
             bool ok = true;
             uint32_t last_bar = 0, last_par = 0;
-            for (int i = 0; i < my_blocks && ok; ++i) {
+            for (int i = 0; i < my_units && ok; ++i) {
                 const int ab = i % C::A_BUFS;
                 if (!mbar_wait(smem_u32(&sh.a_full[ab]), (uint32_t)(i / C::A_BUFS) & 1u, abort_flag, kWaitLimitNs)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a_hi = smem_u32(Abase + ab * C::A_BUF_BYTES);
-                const uint32_t a_lo = a_hi + C::A_SPLIT_BYTES;
+                const uint32_t abuf = smem_u32(Abase + ab * C::A_BUF_BYTES);
                 for (int j = 0; j < nt; ++j, ++gb, ++gacc) {
                     const int s = gb % C::B_STAGES;
                     if (!mbar_wait(smem_u32(&sh.b_full[s]), (uint32_t)(gb / C::B_STAGES) & 1u, abort_flag,
@@ -281,19 +345,20 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                     }
                     tc_fence_after();
                     const uint32_t bsm = smem_u32(Bbase + s * C::B_STAGE_BYTES);
-                    const uint32_t d = tmem + (uint32_t)(acc * BN);
-                    uint32_t accum = 0;
 #pragma unroll
                     for (int split = 0; split < 2; ++split) {
-                        const uint32_t asm_base = split ? a_lo : a_hi;
 #pragma unroll
                         for (int kc = 0; kc < C::KC; ++kc) {
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk) {
-                                const uint64_t ad = sw128_desc(asm_base + kc * (BM * 128) + kk * 32);
                                 const uint64_t bd = sw128_desc(bsm + kc * (BN * 128) + kk * 32);
-                                mma_bf16(d, ad, bd, idesc, accum);
-                                accum = 1;
+                                const uint32_t accum = (split | kc | kk) ? 1u : 0u;
+#pragma unroll
+                                for (int rb = 0; rb < RB; ++rb) {
+                                    const uint32_t apart = abuf + (uint32_t)((rb * 2 + split) * C::A_PART_BYTES);
+                                    const uint64_t ad = sw128_desc(apart + kc * (BM * 128) + kk * 32);
+                                    mma_bf16(tmem + (uint32_t)(acc * RB * BN + rb * BN), ad, bd, idesc, accum);
+                                }
                             }
                         }
                     }
@@ -315,9 +380,9 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
             }
         }
     } else if (warp < 4) {
-        // ---- A builders: z = y (.) x(c) split into bf16 hi / lo, swizzled ----
-        const int aw = warp - 2;  // 0 or 1: even / odd rows
-        for (int i = 0; i < my_blocks; ++i) {
+        // ---- A builders: warp 2 builds row block 0, warp 3 row block 1 of each unit ----
+        const int rb = warp - 2;
+        for (int i = 0; i < my_units; ++i) {
             const int ab = i % C::A_BUFS;
             bool ok = mbar_wait(smem_u32(&sh.a_empty[ab]), ((uint32_t)(i / C::A_BUFS) & 1u) ^ 1u, abort_flag,
                                 kWaitLimitNs);
@@ -326,52 +391,102 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                 if (lane == 0) record_abort(sh, c);
                 break;
             }
-            const int rb = (int)blockIdx.x + i * (int)gridDim.x;
-            uint8_t *Ahi = Abase + ab * C::A_BUF_BYTES;
-            uint8_t *Alo = Ahi + C::A_SPLIT_BYTES;
-            for (int r = aw; r < BM; r += 2) {
-                const int row = rb * BM + r;
-                uint32_t hi[N / 32], lo[N / 32];  // N/32 elements per lane
+            const int unit = (int)blockIdx.x + i * (int)gridDim.x;
+            const int row0 = unit * UM + rb * BM;
+            // each lane gathers the frame and centre of 4 rows at once
+            int fr[4];
+            uint64_t cwl[4][W];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = row0 + q * 32 + lane;
+                fr[q] = -1;
+#pragma unroll
+                for (int w = 0; w < W; ++w) cwl[q][w] = 0;
                 if (row < nrows) {
                     const int t = a.rows ? a.rows[row] : row;
-                    const int frame = a.row_frame ? a.row_frame[row] : a.slot_frame[t / a.L];
-                    const float *yr = a.y + (int64_t)frame * N;
+                    fr[q] = a.row_frame ? a.row_frame[row] : a.slot_frame[t / a.L];
                     const uint64_t *cw = a.cw + (int64_t)t * W;
 #pragma unroll
-                    for (int e = 0; e < N / 32; ++e) {
-                        const int j = lane * (N / 32) + e;
-                        const float v = grid_f(yr[j]);
-                        const float z = ((cw[j >> 6] >> (j & 63)) & 1ull) ? -v : v;
-                        split_bf16(z, hi[e], lo[e]);
-                    }
-                } else {
+                    for (int w = 0; w < W; ++w) cwl[q][w] = cw[w];
+                }
+            }
+            uint8_t *Ahi = Abase + ab * C::A_BUF_BYTES + (rb * 2 + 0) * C::A_PART_BYTES;
+            uint8_t *Alo = Abase + ab * C::A_BUF_BYTES + (rb * 2 + 1) * C::A_PART_BYTES;
+            const int j0 = lane * EPL;  // this lane's elements of every row
+            const int kcl = j0 / 64, e64 = j0 % 64;
+            const int unit16 = e64 / 8, within = (e64 % 8) * 2;
+#pragma unroll 1
+            for (int q = 0; q < 4; ++q) {
+                // rows q*32 .. q*32+31: their frame and centre sit in lane (r % 32), slot q
+                const int frq = q == 0 ? fr[0] : q == 1 ? fr[1] : q == 2 ? fr[2] : fr[3];
+                uint64_t cq0 = q == 0 ? cwl[0][0] : q == 1 ? cwl[1][0] : q == 2 ? cwl[2][0] : cwl[3][0];
+                uint64_t cq1 = q == 0 ? cwl[0][W - 1] : q == 1 ? cwl[1][W - 1] : q == 2 ? cwl[2][W - 1] : cwl[3][W - 1];
+#pragma unroll 1
+                for (int g0 = 0; g0 < 32; g0 += C::G) {
+                    float v[C::G][EPL];
 #pragma unroll
-                    for (int e = 0; e < N / 32; ++e) hi[e] = lo[e] = 0;
+                    for (int u = 0; u < C::G; ++u) {
+                        const int f = __shfl_sync(0xffffffffu, frq, g0 + u);
+                        if (f >= 0) {
+                            const float *yr = a.y + (int64_t)f * N + j0;
+                            if constexpr (EPL == 2) {
+                                const float2 t2 = *reinterpret_cast<const float2 *>(yr);
+                                v[u][0] = t2.x;
+                                v[u][1] = t2.y;
+                            } else {
+                                const float4 t4 = *reinterpret_cast<const float4 *>(yr);
+                                v[u][0] = t4.x;
+                                v[u][1] = t4.y;
+                                v[u][2] = t4.z;
+                                v[u][3] = t4.w;
+                            }
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < EPL; ++e) v[u][e] = 0.0f;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < C::G; ++u) {
+                        const int r = q * 32 + g0 + u;
+                        // both words come from the row's owner lane; this lane keeps its chunk's word
+                        uint64_t bits = __shfl_sync(0xffffffffu, cq0, g0 + u);
+                        if constexpr (W > 1) {
+                            const uint64_t hi_word = __shfl_sync(0xffffffffu, cq1, g0 + u);
+                            bits = kcl ? hi_word : bits;
+                        }
+                        uint32_t hi[EPL], lo[EPL];
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) {
+                            const float y = grid_f(v[u][e]);
+                            const float z = ((bits >> ((j0 + e) & 63)) & 1ull) ? -y : y;
+                            split_bf16(z, hi[e], lo[e]);
+                        }
+                        // element j of row r: chunk j/64, 16-B unit (j%64)/8 stored at unit ^ (r%8)
+                        const int off =
+                            kcl * (BM * 128) + (r / 8) * 1024 + (r % 8) * 128 + ((unit16 ^ (r % 8)) * 16) + within;
+                        if constexpr (EPL == 2) {
+                            *(uint32_t *)(Ahi + off) = hi[0] | (hi[1] << 16);
+                            *(uint32_t *)(Alo + off) = lo[0] | (lo[1] << 16);
+                        } else {
+                            *(uint2 *)(Ahi + off) = make_uint2(hi[0] | (hi[1] << 16), hi[2] | (hi[3] << 16));
+                            *(uint2 *)(Alo + off) = make_uint2(lo[0] | (lo[1] << 16), lo[2] | (lo[3] << 16));
+                        }
+                    }
                 }
-                // element j of row r: chunk j/64, 16-B unit (j%64)/8 stored at unit ^ (r%8)
-                const int j0 = lane * (N / 32);
-                const int kc = j0 / 64, e64 = j0 % 64;
-                const int unit = e64 / 8, within = (e64 % 8) * 2;
-                const int off = kc * (BM * 128) + (r / 8) * 1024 + (r % 8) * 128 + ((unit ^ (r % 8)) * 16) + within;
-                if constexpr (N == 64) {
-                    *(uint32_t *)(Ahi + off) = hi[0] | (hi[1] << 16);
-                    *(uint32_t *)(Alo + off) = lo[0] | (lo[1] << 16);
-                } else {
-                    *(uint2 *)(Ahi + off) = make_uint2(hi[0] | (hi[1] << 16), hi[2] | (hi[3] << 16));
-                    *(uint2 *)(Alo + off) = make_uint2(lo[0] | (lo[1] << 16), lo[2] | (lo[3] << 16));
-                }
+                (void)cq1;
             }
             fence_proxy_async();
             mbar_arrive(smem_u32(&sh.a_full[ab]));
         }
     } else {
-        // ---- epilogue: TMEM -> registers -> running top-K per row ----
+        // ---- epilogue: TMEM -> registers -> running top-K, one row per thread ----
         const int q = warp & 3;              // TMEM lane quadrant
-        const int r = q * 32 + lane;         // row within the block
+        const int rb = (warp - 4) >> 2;      // row block of this warp
+        const int r = q * 32 + lane;         // row within the row block
         int gacc = 0;
         bool ok = true;
-        for (int i = 0; i < my_blocks && ok; ++i) {
-            const int rb = (int)blockIdx.x + i * (int)gridDim.x;
+        for (int i = 0; i < my_units && ok; ++i) {
+            const int unit = (int)blockIdx.x + i * (int)gridDim.x;
             float tv[kTopK];
             int ti[kTopK];
 #pragma unroll
@@ -388,33 +503,28 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                     break;
                 }
                 tc_fence_after();
-                const int col0 = j * BN;
+                const bool full = (j + 1) * BN <= P;
 #pragma unroll 1
-                for (int ch = 0; ch < BN / 32; ++ch) {
-                    uint32_t v[32];
+                for (int ch = 0; ch < BN / 64; ++ch) {
+                    uint32_t v[64];
                     __syncwarp();
-                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + ch * 32), v);
-                    const int cbase = col0 + ch * 32;
-                    float mn = CUDART_INF_F;
-                    const bool full = cbase + 32 <= P;
+                    tmem_ld64(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * RB * BN + rb * BN + ch * 64), v);
+                    const int cbase = j * BN + ch * 64;
+                    if (!full) {
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const float s = __uint_as_float(v[e]);
-                        mn = (full || cbase + e < P) ? fminf(mn, s) : mn;
+                        for (int e = 0; e < 64; ++e)
+                            if (cbase + e >= P) v[e] = __float_as_uint(CUDART_INF_F);
                     }
-                    if (mn < tv[kTopK - 1]) {
-#pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            const float s = __uint_as_float(v[e]);
-                            if ((full || cbase + e < P) && s < tv[kTopK - 1]) topk_insert<kTopK>(tv, ti, s, cbase + e);
-                        }
-                    }
+                    float gm[8];
+                    group_mins<0>(v, gm);
+                    const float m = fmin3(fmin3(gm[0], gm[1], gm[2]), fmin3(gm[3], gm[4], gm[5]), fminf(gm[6], gm[7]));
+                    if (m < tv[kTopK - 1]) scan_groups<0>(v, gm, tv, ti, cbase);
                 }
                 tc_fence_before();
                 mbar_arrive(smem_u32(&sh.acc_empty[acc]));
             }
             if (!ok) break;
-            const int row = rb * BM + r;
+            const int row = unit * UM + rb * BM + r;
             if (row < nrows) {
 #pragma unroll
                 for (int k = 0; k < kTopK; ++k) {
@@ -440,7 +550,7 @@ cudaError_t launch_n(const CodeDev &c, const ScoreArgs &a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(score_tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int64_t grid = c.num_sms;
-    if (!a.n_rows_dev) grid = std::min<int64_t>(grid, (a.n_rows + BM - 1) / BM);
+    if (!a.n_rows_dev) grid = std::min<int64_t>(grid, (a.n_rows + UM - 1) / UM);
     if (grid <= 0) return cudaSuccess;
     score_tc_kernel<N><<<(unsigned)grid, kThreads, smem, s>>>(a, c);
     return cudaGetLastError();

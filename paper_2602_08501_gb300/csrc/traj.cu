@@ -92,22 +92,23 @@ __global__ void __launch_bounds__(kHopThreads) hop_kernel(const Workspace ws, co
     }
 }
 
-// One warp per overflowing row: exact FP64 score of every pattern, argmin with
+// One CTA per overflowing row: exact FP64 score of every pattern, argmin with
 // the lowest index on ties, then the same decision as the hop kernel.
 __global__ void __launch_bounds__(kHopThreads) rescan_kernel(const Workspace ws, const CodeDev c, int iter, int L,
                                                              const float *y) {
+    __shared__ double s_best[kHopThreads / 32];
+    __shared__ int s_idx[kHopThreads / 32];
     const int nres = ws.counters[32 + iter];
     int *act_out = ws.act[(iter + 1) & 1];
     int *n_out = ws.counters + 1 + iter + 1;
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nres; i += warps) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = blockIdx.x; i < nres; i += gridDim.x) {
         const int t = ws.rescan_rows[i];
         const float *yr = y + (int64_t)ws.slot_frame[t / L] * c.n;
         const uint64_t *cw = ws.traj_cw + (int64_t)t * c.W;
         double best = CUDART_INF;
         int bp = -1;
-        for (int p = lane; p < (int)c.P; p += 32) {
+        for (int p = threadIdx.x; p < (int)c.P; p += blockDim.x) {
             const double s = exact_score(yr, cw, c.pat_bits + (int64_t)p * c.W, c.W);
             if (s < best) {
                 best = s;
@@ -124,6 +125,18 @@ __global__ void __launch_bounds__(kHopThreads) rescan_kernel(const Workspace ws,
             }
         }
         if (lane == 0) {
+            s_best[wid] = best;
+            s_idx[wid] = bp;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                const int op = s_idx[w];
+                if (op >= 0 && (s_best[w] < best || (s_best[w] == best && (bp < 0 || op < bp)))) {
+                    best = s_best[w];
+                    bp = op;
+                }
+            }
             ws.traj_state[t] |= kTrajRescan;
             atomicAdd(&c.stats->rescans, 1ull);
             if (apply_decision(ws, c, t, bp, best)) {
@@ -131,6 +144,7 @@ __global__ void __launch_bounds__(kHopThreads) rescan_kernel(const Workspace ws,
                 atomicAdd(&c.stats->hops, 1ull);
             }
         }
+        __syncthreads();
     }
 }
 
