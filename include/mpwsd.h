@@ -229,14 +229,17 @@ MPWSD_API int mpwsd_stage1_list(mpwsd_code *code, const float *y_dev, int64_t B,
  * mpwsd_score_topk -- the scoring step of stage 2 alone: for each row r,
  * the trajectory centre c_r (frame frame_dev[r] of y_dev) gets the scores
  * S(r, p) = sum_{j in supp p} y_j x_j(c_r) for every pattern p (-G/2 of
- * Eq. (5); ED(c xor p) - ED(c) = 4 S), and the MPWSD_TOPK smallest are
- * returned in ascending order (equal scores in ascending pattern index).
- * Scores are the kernel's approximations (mode BF16X2 or FP32), not exact.
+ * Eq. (5); ED(c xor p) - ED(c) = 4 S). Scores are the kernel's
+ * approximations S~ (mode BF16X2 or FP32), each within eps = 2^-14 ||y||_1 of
+ * the exact one. Returned, in ascending order: the MPWSD_TOPK smallest S~ among
+ * the patterns with S~ <= min S~ + 2 eps, i.e. every pattern that can be the
+ * exact minimum unless MPWSD_TOPK of them fill the list (then the list's last
+ * value is within 2 eps of its first, which the caller reads as "rescan").
  *
  *   y_dev       device, B x n FP32.       frame_dev  device, M int32 in [0, B).
  *   cw_dev      device, M x W uint64.     M          rows, >= 0.
  *   topk_val_dev device, M x MPWSD_TOPK FP32; topk_idx_dev device, M x
- *   MPWSD_TOPK int32 (-1 where fewer than MPWSD_TOPK patterns exist).
+ *   MPWSD_TOPK int32 (-1 in the unused tail slots).
  * Asynchronous.
  */
 MPWSD_API int mpwsd_score_topk(mpwsd_code *code, int score_mode, const float *y_dev, int64_t B, const int32_t *frame_dev,

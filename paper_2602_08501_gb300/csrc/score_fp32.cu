@@ -4,8 +4,9 @@
 // pattern p of the sphere S_r(0) \ {0}, the score is
 //     S(p) = sum_{j in supp p} z_j,   z_j = y_j x_j(c),  x = 1 - 2c,
 // i.e. -G(p)/2 with G the correlation gain of Eq. (5); ED(c xor p) - ED(c)
-// = 4 S(p) (translation identity, Eq. (3)). The kernel keeps the K smallest
-// scores of each row with their pattern indices and never writes S itself.
+// = 4 S(p) (translation identity, Eq. (3)). The kernel keeps, per row, the K
+// smallest scores that lie within 2 eps of the row's smallest (eps the re-rank
+// margin) with their pattern indices, and never writes S itself.
 //
 // Mapping: one thread per row, 128 rows per CTA. The CTA stages its rows'
 // z vectors in shared memory (row stride n+1 floats: conflict-free per-thread
@@ -40,6 +41,7 @@ __global__ void __launch_bounds__(kRows) score_fp32_kernel(const ScoreArgs a, co
         const int r = rb * kRows + tid;
         const bool live = r < nrows;
         __syncthreads();
+        float l1 = 0.0f;
         if (live) {
             const int t = a.rows ? a.rows[r] : r;
             const int frame = a.row_frame ? a.row_frame[r] : a.slot_frame[t / a.L];
@@ -51,6 +53,7 @@ __global__ void __launch_bounds__(kRows) score_fp32_kernel(const ScoreArgs a, co
 #pragma unroll 8
                 for (int b = 0; b < 64 && w * 64 + b < N; ++b) {
                     const float v = grid_f(yr[w * 64 + b]);
+                    l1 += fabsf(v);
                     zr[w * 64 + b] = ((bits >> b) & 1ull) ? -v : v;
                 }
             }
@@ -65,6 +68,9 @@ __global__ void __launch_bounds__(kRows) score_fp32_kernel(const ScoreArgs a, co
             tv[q] = CUDART_INF_F;
             ti[q] = -1;
         }
+        // admission threshold: below the K-th best kept and within 2 eps of the best kept
+        const float eps2 = __fmul_ru(2.0f * kEpsScale, __fmul_ru(l1, 1.0f + 1.0f / 1024.0f));
+        float thr = CUDART_INF_F;
         for (int p0 = 0; p0 < P; p0 += kPatTile) {
             const int np = min(kPatTile, P - p0);
             __syncthreads();
@@ -83,7 +89,10 @@ __global__ void __launch_bounds__(kRows) score_fp32_kernel(const ScoreArgs a, co
                     s += zr[(w4 >> 16) & 255u];
                     s += zr[w4 >> 24];
                 }
-                if (s < tv[kTopK - 1]) topk_insert<kTopK>(tv, ti, s, p0 + p);
+                if (s < thr) {
+                    topk_insert<kTopK>(tv, ti, s, p0 + p);
+                    thr = fminf(tv[kTopK - 1], __fadd_ru(tv[0], eps2));
+                }
             }
         }
         if (live) {

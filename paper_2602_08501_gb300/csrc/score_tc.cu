@@ -173,17 +173,25 @@ __device__ __forceinline__ float min8(const uint32_t (&v)[64]) {
                  fminf(__uint_as_float(v[8 * G8 + 6]), __uint_as_float(v[8 * G8 + 7])));
 }
 
-// Move every value of group G8 that beats the row's current K-th best into
-// the running top-K: take the group minimum, insert it (its lowest position on
-// ties), blank it, repeat. Usually zero or one round.
+// Current admission threshold of a row: a value enters the running list only
+// if it beats the K-th best kept so far and lies within 2 eps of the best kept
+// so far (anything above that band can never be a candidate of the re-rank).
+__device__ __forceinline__ float admit_thr(const float (&tv)[kTopK], float eps2) {
+    return fminf(tv[kTopK - 1], __fadd_ru(tv[0], eps2));
+}
+
+// Move every value of group G8 below the admission threshold into the running
+// list: take the group minimum, insert it (its lowest position on ties), blank
+// it, repeat. Usually zero or one round.
 template <int G8>
 __device__ __forceinline__ void drain_group(uint32_t (&v)[64], float gm, float (&tv)[kTopK], int (&ti)[kTopK],
-                                            int cbase) {
-    while (gm < tv[kTopK - 1]) {
+                                            float &thr, float eps2, int cbase) {
+    while (gm < thr) {
         int pos = 7;
 #pragma unroll
         for (int e = 6; e >= 0; --e) pos = (__uint_as_float(v[8 * G8 + e]) == gm) ? e : pos;
         topk_insert<kTopK>(tv, ti, gm, cbase + 8 * G8 + pos);
+        thr = admit_thr(tv, eps2);
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[8 * G8 + e] = (e == pos) ? __float_as_uint(CUDART_INF_F) : v[8 * G8 + e];
         gm = min8<G8>(v);
@@ -192,10 +200,10 @@ __device__ __forceinline__ void drain_group(uint32_t (&v)[64], float gm, float (
 
 template <int G8>
 __device__ __forceinline__ void scan_groups(uint32_t (&v)[64], const float (&gm)[8], float (&tv)[kTopK],
-                                            int (&ti)[kTopK], int cbase) {
+                                            int (&ti)[kTopK], float &thr, float eps2, int cbase) {
     if constexpr (G8 < 8) {
-        if (gm[G8] < tv[kTopK - 1]) drain_group<G8>(v, gm[G8], tv, ti, cbase);
-        scan_groups<G8 + 1>(v, gm, tv, ti, cbase);
+        if (gm[G8] < thr) drain_group<G8>(v, gm[G8], tv, ti, thr, eps2, cbase);
+        scan_groups<G8 + 1>(v, gm, tv, ti, thr, eps2, cbase);
     }
 }
 
@@ -487,6 +495,7 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
         bool ok = true;
         for (int i = 0; i < my_units && ok; ++i) {
             const int unit = (int)blockIdx.x + i * (int)gridDim.x;
+            const int row = unit * UM + rb * BM + r;
             float tv[kTopK];
             int ti[kTopK];
 #pragma unroll
@@ -494,6 +503,21 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                 tv[k] = CUDART_INF_F;
                 ti[k] = -1;
             }
+            // 2 eps of this row (the re-rank margin), from ||y||_1 of its frame
+            float eps2 = 0.0f;
+            if (row < nrows) {
+                const int t = a.rows ? a.rows[row] : row;
+                const int f = a.row_frame ? a.row_frame[row] : a.slot_frame[t / a.L];
+                const float4 *y4 = reinterpret_cast<const float4 *>(a.y + (int64_t)f * N);
+                float l1 = 0.0f;
+#pragma unroll 4
+                for (int k4 = 0; k4 < N / 4; ++k4) {
+                    const float4 q4 = y4[k4];
+                    l1 += fabsf(grid_f(q4.x)) + fabsf(grid_f(q4.y)) + fabsf(grid_f(q4.z)) + fabsf(grid_f(q4.w));
+                }
+                eps2 = __fmul_ru(2.0f * kEpsScale, __fmul_ru(l1, 1.0f + 1.0f / 1024.0f));
+            }
+            float thr = CUDART_INF_F;
             for (int j = 0; j < nt; ++j, ++gacc) {
                 const int acc = gacc & 1;
                 bool w = mbar_wait(smem_u32(&sh.acc_full[acc]), (uint32_t)(gacc >> 1) & 1u, abort_flag, kWaitLimitNs);
@@ -518,13 +542,12 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                     float gm[8];
                     group_mins<0>(v, gm);
                     const float m = fmin3(fmin3(gm[0], gm[1], gm[2]), fmin3(gm[3], gm[4], gm[5]), fminf(gm[6], gm[7]));
-                    if (m < tv[kTopK - 1]) scan_groups<0>(v, gm, tv, ti, cbase);
+                    if (m < thr) scan_groups<0>(v, gm, tv, ti, thr, eps2, cbase);
                 }
                 tc_fence_before();
                 mbar_arrive(smem_u32(&sh.acc_empty[acc]));
             }
             if (!ok) break;
-            const int row = unit * UM + rb * BM + r;
             if (row < nrows) {
 #pragma unroll
                 for (int k = 0; k < kTopK; ++k) {
