@@ -36,20 +36,24 @@ __device__ __forceinline__ void topk_insert(float (&v)[K], int (&ix)[K], float s
     }
 }
 
-// Exact score S = sum_{j in supp p} y_j x_j(c) in FP64 (exact on the grid).
+// Exact score S = sum_{j in supp p} y_j x_j(c), returned in FP64. The terms
+// are grid integers round(y 2^19) (|.| < 2^23) and at most 128 of them are
+// added, so the sum is accumulated exactly in int32 and converted once; this is
+// the same number an FP64 summation gives (exact on the grid) at a fraction of
+// the FP64-pipe work.
 __device__ __forceinline__ double exact_score(const float *yr, const uint64_t *c, const uint64_t *p, int W) {
-    double s = 0.0;
+    int s = 0;
     for (int w = 0; w < W; ++w) {
         uint64_t m = p[w];
         const uint64_t cw = c[w];
         while (m) {
             const int b = __ffsll((long long)m) - 1;
             m &= m - 1;
-            const double v = (double)grid_q(yr[w * 64 + b]) * (1.0 / 524288.0);
+            const int v = grid_q(yr[w * 64 + b]);
             s += ((cw >> b) & 1ull) ? -v : v;
         }
     }
-    return s;
+    return (double)s * (1.0 / 524288.0);
 }
 
 // Warp-aggregated append: every lane of `mask` calls this; lanes with pred
@@ -63,6 +67,63 @@ __device__ __forceinline__ int append_slot(unsigned mask, int *counter, bool pre
     if (lane == leader) base = atomicAdd(counter, __popc(ballot));
     base = __shfl_sync(ballot, base, leader);
     return base + __popc(ballot & ((1u << lane) - 1u));
+}
+
+// Decision of Algorithm 1 for trajectory t: hop to c xor p when the exact score
+// S < 0 (a strict ED decrease of 4|S|), else deactivate. Returns true on a hop.
+__device__ __forceinline__ bool apply_decision(const Workspace &ws, const CodeDev &c, int t, int p, double S) {
+    const int W = c.W;
+    if (p >= 0 && S < 0.0) {
+        uint64_t *cw = ws.traj_cw + (int64_t)t * W;
+        const uint64_t *pb = c.pat_bits + (int64_t)p * W;
+        for (int w = 0; w < W; ++w) cw[w] ^= pb[w];
+        ws.traj_D[t] += 2.0 * S;
+        ws.traj_state[t] += 1u;  // hops counter in the low byte (<= MPWSD_MAX_T)
+        return true;
+    }
+    return false;
+}
+
+enum RowOutcome { kRowNone = 0, kRowHop = 1, kRowStop = 2, kRowRescan = 3 };
+
+// Near-tie re-rank of one trajectory after its scoring step: the kernel kept
+// candidates (v, ix) ascending, every pattern whose approximate score is within
+// 2 eps of the smallest (eps = 2^-14 ||y||_1 of the frame). Each of them is
+// re-scored exactly in FP64; the smallest exact score (lowest index on ties)
+// decides the hop. If all kTopK slots lie within the band, more candidates may
+// exist and the row goes to the full FP64 rescan.
+__device__ __forceinline__ int resolve_row(const Workspace &ws, const CodeDev &c, int t, int L, const float *y,
+                                           const float (&v)[kTopK], const int (&ix)[kTopK],
+                                           unsigned long long &cand) {
+    const int slot = t / L;
+    const float *yr = y + (int64_t)ws.slot_frame[slot] * c.n;
+    const float eps = kEpsScale * ws.slot_l1[slot];
+    const float thr = __fadd_ru(v[0], __fmul_ru(2.0f, eps));
+    if (ix[kTopK - 1] >= 0 && v[kTopK - 1] <= thr) return kRowRescan;
+    double best = CUDART_INF;
+    int bp = -1;
+    const uint64_t *cw = ws.traj_cw + (int64_t)t * c.W;
+#pragma unroll
+    for (int q = 0; q < kTopK; ++q) {
+        if (ix[q] >= 0 && v[q] <= thr) {
+            const double s = exact_score(yr, cw, c.pat_bits + (int64_t)ix[q] * c.W, c.W);
+            ++cand;
+            if (s < best || (s == best && ix[q] < bp)) {
+                best = s;
+                bp = ix[q];
+            }
+        }
+    }
+    return apply_decision(ws, c, t, bp, best) ? kRowHop : kRowStop;
+}
+
+// Append trajectory t to the next active list (hop) or the rescan list, with
+// warp-aggregated atomics; every lane of the warp calls this together.
+__device__ __forceinline__ void route_row(const Workspace &ws, int iter, int outcome, int t) {
+    const int po = append_slot(0xffffffffu, ws.counters + 1 + iter + 1, outcome == kRowHop);
+    if (po >= 0) ws.act[(iter + 1) & 1][po] = t;
+    const int pr = append_slot(0xffffffffu, ws.counters + 32 + iter, outcome == kRowRescan);
+    if (pr >= 0) ws.rescan_rows[pr] = t;
 }
 
 }  // namespace mpwsd

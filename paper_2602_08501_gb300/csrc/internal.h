@@ -100,9 +100,14 @@ struct ScoreArgs {
     const int *slot_frame;    // frame of trajectory id t = slot_frame[t / L] (decode) ...
     const int32_t *row_frame; // ... or frame of row r = row_frame[r] (direct)
     int L;
-    float *topk_val;          // row-indexed
+    float *topk_val;          // row-indexed (direct mode)
     int *topk_idx;
     unsigned long long *evals; // stats counter (may be null)
+    // decode mode: the scoring kernel finishes each row with the FP64 re-rank
+    // and the hop of Algorithm 1 (fused = 1) instead of writing its top-K
+    int fused;
+    int iter;
+    Workspace ws;
 };
 
 // Launchers (return cudaError_t of the launch).

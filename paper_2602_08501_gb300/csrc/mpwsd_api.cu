@@ -482,12 +482,13 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
         a.L = L;
         a.topk_val = ws.topk_val;
         a.topk_idx = ws.topk_idx;
+        a.fused = 1;  // the scoring kernel re-ranks, hops and compacts each row itself
+        a.iter = it;
+        a.ws = ws;
         e = launch_score(code, o.score_mode, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "scoring launch");
-        e = timed_launch(code, MPWSD_KERNEL_HOP, s, [&] { return launch_hop(d, ws, it, L, y_dev, s); });
-        if (e == cudaSuccess)
-            e = timed_launch(code, MPWSD_KERNEL_RESCAN, s, [&] { return launch_rescan(d, ws, it, L, y_dev, s); });
-        if (e != cudaSuccess) return cuda_fail(e, "hop launch");
+        e = timed_launch(code, MPWSD_KERNEL_RESCAN, s, [&] { return launch_rescan(d, ws, it, L, y_dev, s); });
+        if (e != cudaSuccess) return cuda_fail(e, "rescan launch");
     }
     e = timed_launch(code, MPWSD_KERNEL_FINAL, s, [&] { return launch_final(d, ws, L, T, B, cw_dev, flags_dev, s); });
     if (e != cudaSuccess) return cuda_fail(e, "final launch");

@@ -135,17 +135,42 @@ __device__ __forceinline__ uint64_t info_leaf(SclCtx<FZ> &cx, PathState<N> &st) 
     } else {
         const long long a = lam < 0 ? -(long long)lam : (long long)lam;
         const bool valid = cx.lane < cx.count;
-        const unsigned long long base = ((unsigned long long)cx.lane << 1);
-        // key = (metric, parent position, bit); unique per child
-        const unsigned long long k0 = valid ? (((unsigned long long)st.pm << 6) | base | hd) : ~0ull;
-        const unsigned long long k1 = valid ? (((unsigned long long)(st.pm + a) << 6) | base | (hd ^ 1u)) : ~0ull;
+        // Rank of each child under the key (metric, parent position, bit). Metrics
+        // are taken relative to the frame's best path; when every relative
+        // metric of the warp fits 25 bits the keys fit 32 bits (the usual case),
+        // otherwise the same ranking runs on 64-bit keys.
+        long long pmin = valid ? st.pm : 0x7fffffffffffffffLL;
+#pragma unroll
+        for (int o = LW / 2; o >= 1; o >>= 1) pmin = min(pmin, __shfl_xor_sync(kFull, pmin, o, LW));
+        const long long d0 = st.pm - pmin;
+        const bool small = !valid || d0 + a < (1LL << 25);
         int r0 = 0, r1 = 0;
+        unsigned long long k0, k1;
+        if (__all_sync(kFull, small)) {
+            const uint32_t base32 = (uint32_t)cx.lane << 1;
+            const uint32_t q0 = valid ? (((uint32_t)d0 << 6) | base32 | hd) : 0xffffffffu;
+            const uint32_t q1 = valid ? (((uint32_t)(d0 + a) << 6) | base32 | (hd ^ 1u)) : 0xffffffffu;
 #pragma unroll 4
-        for (int s = 0; s < LW; ++s) {
-            const unsigned long long s0 = __shfl_sync(kFull, k0, s, LW);
-            const unsigned long long s1 = __shfl_sync(kFull, k1, s, LW);
-            r0 += (s0 < k0) + (s1 < k0);
-            r1 += (s0 < k1) + (s1 < k1);
+            for (int s = 0; s < LW; ++s) {
+                const uint32_t s0 = __shfl_sync(kFull, q0, s, LW);
+                const uint32_t s1 = __shfl_sync(kFull, q1, s, LW);
+                r0 += (s0 < q0) + (s1 < q0);
+                r1 += (s0 < q1) + (s1 < q1);
+            }
+            // back to absolute 64-bit keys for the exchange
+            k0 = valid ? ((((unsigned long long)st.pm) << 6) | (q0 & 63u)) : ~0ull;
+            k1 = valid ? ((((unsigned long long)(st.pm + a)) << 6) | (q1 & 63u)) : ~0ull;
+        } else {
+            const unsigned long long base = ((unsigned long long)cx.lane << 1);
+            k0 = valid ? (((unsigned long long)st.pm << 6) | base | hd) : ~0ull;
+            k1 = valid ? (((unsigned long long)(st.pm + a) << 6) | base | (hd ^ 1u)) : ~0ull;
+#pragma unroll 4
+            for (int s = 0; s < LW; ++s) {
+                const unsigned long long s0 = __shfl_sync(kFull, k0, s, LW);
+                const unsigned long long s1 = __shfl_sync(kFull, k1, s, LW);
+                r0 += (s0 < k0) + (s1 < k0);
+                r1 += (s0 < k1) + (s1 < k1);
+            }
         }
         const int nc = min(2 * cx.count, cx.L);
         if (r0 < nc) cx.xchg[r0] = k0;

@@ -6,7 +6,8 @@
 // i.e. -G(p)/2 with G the correlation gain of Eq. (5); ED(c xor p) - ED(c)
 // = 4 S(p) (translation identity, Eq. (3)). The kernel keeps, per row, the K
 // smallest scores that lie within 2 eps of the row's smallest (eps the re-rank
-// margin) with their pattern indices, and never writes S itself.
+// margin) with their pattern indices, never writes S itself, and in a decode
+// finishes each row with the FP64 re-rank and the hop.
 //
 // Mapping: one thread per row, 128 rows per CTA. The CTA stages its rows'
 // z vectors in shared memory (row stride n+1 floats: conflict-free per-thread
@@ -37,6 +38,7 @@ __global__ void __launch_bounds__(kRows) score_fp32_kernel(const ScoreArgs a, co
     const int nblk = (nrows + kRows - 1) / kRows;
     const int tid = threadIdx.x;
     float *zr = zs + tid * ZS;
+    unsigned long long my_cand = 0, my_hops = 0;
     for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
         const int r = rb * kRows + tid;
         const bool live = r < nrows;
@@ -95,12 +97,29 @@ __global__ void __launch_bounds__(kRows) score_fp32_kernel(const ScoreArgs a, co
                 }
             }
         }
-        if (live) {
+        if (a.fused) {
+            // finish the row: FP64 re-rank of the kept candidates and the hop (Algorithm 1)
+            int outcome = kRowNone, t = 0;
+            if (live) {
+                t = a.rows[r];
+                outcome = resolve_row(a.ws, c, t, a.L, a.y, tv, ti, my_cand);
+                my_hops += outcome == kRowHop;
+            }
+            route_row(a.ws, a.iter, outcome, t);
+        } else if (live) {
 #pragma unroll
             for (int q = 0; q < kTopK; ++q) {
                 a.topk_val[(int64_t)r * kTopK + q] = tv[q];
                 a.topk_idx[(int64_t)r * kTopK + q] = ti[q];
             }
+        }
+    }
+    if (a.fused) {
+        const unsigned long long wc = __reduce_add_sync(0xffffffffu, (unsigned)my_cand);
+        const unsigned long long wh = __reduce_add_sync(0xffffffffu, (unsigned)my_hops);
+        if ((threadIdx.x & 31) == 0) {
+            if (wc) atomicAdd(&c.stats->rerank_candidates, wc);
+            if (wh) atomicAdd(&c.stats->hops, wh);
         }
     }
 }

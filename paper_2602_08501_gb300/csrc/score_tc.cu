@@ -6,8 +6,9 @@
 // S = Z P^T, a dense contraction. z is split as z = hi + lo with hi, lo
 // bf16 (|z - hi - lo| <= 2^-16 |z|), so S ~= [Z_hi | Z_lo] [P | P]^T is two
 // bf16 MMAs per K step into one FP32 accumulator; P is exact in bf16. The
-// epilogue keeps the K smallest scores of each row with their indices, so
-// the score matrix never reaches HBM.
+// epilogue keeps each row's candidates for the exact argmin and, in a decode,
+// finishes the row itself (FP64 re-rank, hop, compaction), so neither the
+// score matrix nor the candidates reach HBM.
 //
 // Kernel shape (sm_103a): persistent, one CTA per SM, 384 threads, units of
 // 256 rows (two 128-row blocks that share every pattern tile, halving the L2
@@ -493,6 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
         const int r = q * 32 + lane;         // row within the row block
         int gacc = 0;
         bool ok = true;
+        unsigned long long my_cand = 0, my_hops = 0;
         for (int i = 0; i < my_units && ok; ++i) {
             const int unit = (int)blockIdx.x + i * (int)gridDim.x;
             const int row = unit * UM + rb * BM + r;
@@ -548,7 +550,16 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                 mbar_arrive(smem_u32(&sh.acc_empty[acc]));
             }
             if (!ok) break;
-            if (row < nrows) {
+            if (a.fused) {
+                // finish the row: FP64 re-rank of the kept candidates and the hop (Algorithm 1)
+                int outcome = kRowNone, t = 0;
+                if (row < nrows) {
+                    t = a.rows[row];
+                    outcome = resolve_row(a.ws, c, t, a.L, a.y, tv, ti, my_cand);
+                    my_hops += outcome == kRowHop;
+                }
+                route_row(a.ws, a.iter, outcome, t);
+            } else if (row < nrows) {
 #pragma unroll
                 for (int k = 0; k < kTopK; ++k) {
                     a.topk_val[(int64_t)row * kTopK + k] = tv[k];
@@ -557,6 +568,14 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
             }
         }
         if (!ok && lane == 0) record_abort(sh, c);
+        if (a.fused) {
+            const unsigned long long wc = __reduce_add_sync(0xffffffffu, (unsigned)my_cand);
+            const unsigned long long wh = __reduce_add_sync(0xffffffffu, (unsigned)my_hops);
+            if (lane == 0) {
+                if (wc) atomicAdd(&c.stats->rerank_candidates, wc);
+                if (wh) atomicAdd(&c.stats->hops, wh);
+            }
+        }
     }
 
     tc_fence_before();

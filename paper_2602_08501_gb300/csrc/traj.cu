@@ -13,42 +13,21 @@ namespace {
 
 constexpr int kHopThreads = 256;
 
-enum Outcome { kNone = 0, kHop = 1, kStop = 2, kRescan = 3 };
-
-// Apply the decision of Algorithm 1 for trajectory t: hop to c xor p if the
-// exact score S < 0 (strict ED decrease of 4|S|), else deactivate.
-__device__ __forceinline__ bool apply_decision(const Workspace &ws, const CodeDev &c, int t, int p, double S) {
-    const int W = c.W;
-    if (p >= 0 && S < 0.0) {
-        uint64_t *cw = ws.traj_cw + (int64_t)t * W;
-        const uint64_t *pb = c.pat_bits + (int64_t)p * W;
-        for (int w = 0; w < W; ++w) cw[w] ^= pb[w];
-        ws.traj_D[t] += 2.0 * S;
-        ws.traj_state[t] += 1u;  // hops counter in the low byte (<= MPWSD_MAX_T)
-        return true;
-    }
-    return false;
-}
-
+// Re-rank and decision from a top-K written by a scoring kernel (used when the
+// scoring kernel did not finish the rows itself).
 __global__ void __launch_bounds__(kHopThreads) hop_kernel(const Workspace ws, const CodeDev c, int iter, int L,
                                                           const float *y) {
     const int nrows = ws.counters[1 + iter];
     const int *act_in = ws.act[iter & 1];
-    int *act_out = ws.act[(iter + 1) & 1];
-    int *n_out = ws.counters + 1 + iter + 1;
-    int *n_rescan = ws.counters + 32 + iter;
     const int stride = gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     unsigned long long my_cand = 0, my_hops = 0;
     // iterate in whole warps so the aggregated appends see converged lanes
     for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nrows; base += stride) {
         const int r = base + lane;
-        int outcome = kNone, t = 0;
+        int outcome = kRowNone, t = 0;
         if (r < nrows) {
             t = act_in[r];
-            const int slot = t / L;
-            const float *yr = y + (int64_t)ws.slot_frame[slot] * c.n;
-            const float eps = kEpsScale * ws.slot_l1[slot];
             float v[kTopK];
             int ix[kTopK];
 #pragma unroll
@@ -56,33 +35,10 @@ __global__ void __launch_bounds__(kHopThreads) hop_kernel(const Workspace ws, co
                 v[q] = ws.topk_val[(int64_t)r * kTopK + q];
                 ix[q] = ws.topk_idx[(int64_t)r * kTopK + q];
             }
-            const float thr = __fadd_ru(v[0], __fmul_ru(2.0f, eps));
-            if (ix[kTopK - 1] >= 0 && v[kTopK - 1] <= thr) {
-                outcome = kRescan;
-            } else {
-                double best = CUDART_INF;
-                int bp = -1;
-                const uint64_t *cw = ws.traj_cw + (int64_t)t * c.W;
-#pragma unroll
-                for (int q = 0; q < kTopK; ++q) {
-                    if (ix[q] >= 0 && v[q] <= thr) {
-                        const double s = exact_score(yr, cw, c.pat_bits + (int64_t)ix[q] * c.W, c.W);
-                        ++my_cand;
-                        if (s < best || (s == best && ix[q] < bp)) {
-                            best = s;
-                            bp = ix[q];
-                        }
-                    }
-                }
-                const bool hop = apply_decision(ws, c, t, bp, best);
-                outcome = hop ? kHop : kStop;
-                my_hops += hop;
-            }
+            outcome = resolve_row(ws, c, t, L, y, v, ix, my_cand);
+            my_hops += outcome == kRowHop;
         }
-        const int po = append_slot(0xffffffffu, n_out, outcome == kHop);
-        if (po >= 0) act_out[po] = t;
-        const int pr = append_slot(0xffffffffu, n_rescan, outcome == kRescan);
-        if (pr >= 0) ws.rescan_rows[pr] = t;
+        route_row(ws, iter, outcome, t);
     }
     const unsigned long long wc = __reduce_add_sync(0xffffffffu, (unsigned)my_cand);
     const unsigned long long wh = __reduce_add_sync(0xffffffffu, (unsigned)my_hops);
