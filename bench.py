@@ -169,16 +169,16 @@ def src_hash(*rel):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, source_hash: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+def recorded_traffic(kernel: str, source_hash: str, unit: str):
+    """DRAM bytes per unit (row or frame) from the committed ncu summary of this
+    kernel, if it was taken on the current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", f"{kernel}_ncu.md")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         txt = fh.read()
     m_src = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
-    m_b = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    m_b = re.search(rf"dram_bytes_per_{unit}:\s*([0-9.eE+]+)", txt)
     if not m_src or not m_b or m_src.group(1) != source_hash:
         return None
     return float(m_b.group(1))
@@ -369,8 +369,10 @@ def run_ours(args, wl_cfg):
         if kname == "score_tc":
             flops = evals * 2 * n * 2 / launches  # dense bf16 work per launch: 2 n flops x 2 splits per pattern-eval
             ach = flops / per_launch_s / 1e12
-            src = src_hash("paper_2602_08501_gb300/csrc/score_tc.cu")
-            tr = recorded_traffic("score_tc", src)
+            src = src_hash("paper_2602_08501_gb300/csrc/score_tc.cu", "paper_2602_08501_gb300/csrc/common.cuh",
+                           "paper_2602_08501_gb300/csrc/internal.h")
+            bpr = recorded_traffic("score_tc", src, "row")
+            tr = None if bpr is None else bpr * (evals / P) / launches  # scaled by active rows per launch
             return {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_sus"], "unit": "TFLOP/s",
                     "frac": ach / peaks["bf16_sus"], "traffic": tr, "kernel": "score_tc",
                     "peak_kind": f"bf16 sustained, {peaks['source']}", "flops_per_launch": flops}
@@ -383,8 +385,9 @@ def run_ours(args, wl_cfg):
         if kname == "scl":
             ops = frames * 4 * L * n * math.log2(n) / launches  # Table I: (4/3) L log2 N ED units x 3N
             ach = ops / per_launch_s / 1e12
-            src = src_hash("paper_2602_08501_gb300/csrc/scl_impl.cuh")
-            tr = recorded_traffic("scl", src)
+            src = src_hash("paper_2602_08501_gb300/csrc/scl_impl.cuh", "paper_2602_08501_gb300/csrc/internal.h")
+            bpf = recorded_traffic("scl", src, "frame")
+            tr = None if bpf is None else bpf * frames
             return {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "Top/s",
                     "frac": ach / (alu_peak / 1e12), "traffic": tr, "kernel": "scl",
                     "peak_kind": "152 SMs x 128 INT32 lanes x max SM clock", "ops_per_launch": ops}
