@@ -73,6 +73,12 @@ struct CodeDev {
     uint64_t *crc_masks = nullptr;  // crc_len x W, codeword domain: syndrome bit b = parity(c & mask_b)
     DevStats *stats = nullptr;
     int num_sms = 0;
+    // Bounded device waits: a wait that exceeds this records an error and the
+    // kernel exits cleanly. test_stall (set from MPWSD_TEST_TC_STALL when the
+    // code is loaded, tests only) makes the tensor-core kernel's producer issue
+    // no copies, so its consumers' waits run out on purpose.
+    unsigned long long wait_limit_ns = 2000000000ull;
+    int test_stall = 0;
 };
 
 struct SclArgs {

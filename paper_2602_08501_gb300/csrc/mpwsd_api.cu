@@ -222,6 +222,12 @@ extern "C" int mpwsd_load_code(int n, const uint8_t *G, const uint8_t *frozen, i
                 d.frozen_hi |= 1ull << (i - 64);
         }
     d.rm_spec = rm_specialisation(n, d.frozen_lo, d.frozen_hi);
+    if (const char *st = getenv("MPWSD_TEST_TC_STALL")) {
+        if (atoi(st) > 0) {  // test hook: see CodeDev::test_stall
+            d.test_stall = 1;
+            d.wait_limit_ns = 20000000ull;
+        }
+    }
     d.trailing_frozen = info.back() != n - 1;
     d.w_max = w_max;
     d.wq_max = (w_max + 3) / 4;

@@ -44,7 +44,6 @@ constexpr int UM = BM * RB;             // rows per unit
 constexpr int BN = kTcPatternsPerTile;  // patterns per tile (MMA N)
 constexpr int kThreads = 384;                // 12 warps: producer, MMA, 2 builders, 8 epilogue
 constexpr int kEpiThreads = 256;
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: far beyond any legitimate wait
 constexpr unsigned long long kErrTcTimeout = 0x7C01;
 
 template <int N>
@@ -296,14 +295,14 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
 
     if (warp == 0) {
         // ---- producer: pattern tiles into the B ring ----
-        if (lane == 0) {
+        if (lane == 0 && !c.test_stall) {
             int g = 0;
             bool ok = true;
             for (int i = 0; i < my_units && ok; ++i) {
                 for (int j = 0; j < nt; ++j, ++g) {
                     const int s = g % C::B_STAGES;
                     const uint32_t ph = (uint32_t)(g / C::B_STAGES) & 1u;
-                    if (!mbar_wait(smem_u32(&sh.b_empty[s]), ph ^ 1u, abort_flag, kWaitLimitNs)) {
+                    if (!mbar_wait(smem_u32(&sh.b_empty[s]), ph ^ 1u, abort_flag, c.wait_limit_ns)) {
                         ok = false;
                         break;
                     }
@@ -333,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
             uint32_t last_bar = 0, last_par = 0;
             for (int i = 0; i < my_units && ok; ++i) {
                 const int ab = i % C::A_BUFS;
-                if (!mbar_wait(smem_u32(&sh.a_full[ab]), (uint32_t)(i / C::A_BUFS) & 1u, abort_flag, kWaitLimitNs)) {
+                if (!mbar_wait(smem_u32(&sh.a_full[ab]), (uint32_t)(i / C::A_BUFS) & 1u, abort_flag, c.wait_limit_ns)) {
                     ok = false;
                     break;
                 }
@@ -342,13 +341,13 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                 for (int j = 0; j < nt; ++j, ++gb, ++gacc) {
                     const int s = gb % C::B_STAGES;
                     if (!mbar_wait(smem_u32(&sh.b_full[s]), (uint32_t)(gb / C::B_STAGES) & 1u, abort_flag,
-                                   kWaitLimitNs)) {
+                                   c.wait_limit_ns)) {
                         ok = false;
                         break;
                     }
                     const int acc = gacc & 1;
                     if (!mbar_wait(smem_u32(&sh.acc_empty[acc]), ((uint32_t)(gacc >> 1) & 1u) ^ 1u, abort_flag,
-                                   kWaitLimitNs)) {
+                                   c.wait_limit_ns)) {
                         ok = false;
                         break;
                     }
@@ -394,7 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
         for (int i = 0; i < my_units; ++i) {
             const int ab = i % C::A_BUFS;
             bool ok = mbar_wait(smem_u32(&sh.a_empty[ab]), ((uint32_t)(i / C::A_BUFS) & 1u) ^ 1u, abort_flag,
-                                kWaitLimitNs);
+                                c.wait_limit_ns);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
                 if (lane == 0) record_abort(sh, c);
@@ -522,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
             float thr = CUDART_INF_F;
             for (int j = 0; j < nt; ++j, ++gacc) {
                 const int acc = gacc & 1;
-                bool w = mbar_wait(smem_u32(&sh.acc_full[acc]), (uint32_t)(gacc >> 1) & 1u, abort_flag, kWaitLimitNs);
+                bool w = mbar_wait(smem_u32(&sh.acc_full[acc]), (uint32_t)(gacc >> 1) & 1u, abort_flag, c.wait_limit_ns);
                 w = __all_sync(0xffffffffu, w);
                 if (!w) {
                     ok = false;
