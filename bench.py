@@ -439,20 +439,68 @@ def run_ours(args, wl_cfg):
     return line
 
 
+def run_serving(args):
+    """Workload 5: Poisson arrivals of mixed RM(2,6)+CRC-6 / RM(2,7)+CRC-6 frames
+    (50/50), Eb/N0 uniform in [0.5, 3] dB, through the continuous-batching loop;
+    one JSON line with throughput and p50/p99 per-frame latency per arrival rate."""
+    import torch
+
+    import synth
+    from paper_2602_08501_gb300 import mpwsd, serving
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rates = [float(r) * 1e6 for r in args.rates.split(",")]
+    n_max = int(max(rates) * args.serve_seconds / 2) + 1
+    specs = {"rm26": serving.CodeSpec(mpwsd.Code.rm(6, 2, crc_poly=0x21, crc_len=6, weights=[16]), 8, 4),
+             "rm27": serving.CodeSpec(mpwsd.Code.rm(7, 2, crc_poly=0x21, crc_len=6, weights=[32]), 16, 6)}
+    pools = {"rm26": synth.make_workload("rm26_crc6", (0.5, 3.0), n_max, seed=4),
+             "rm27": synth.make_workload("rm27_crc6", (0.5, 3.0), n_max, seed=5)}
+    ys = {nm: torch.from_numpy(pools[nm].y).pin_memory() for nm in specs}
+    srv = serving.Server(specs, max_batch=args.serve_batch, slots_per_code=4, min_batch=args.serve_batch // 8,
+                         max_wait_s=args.serve_wait_us * 1e-6)
+    # warm-up: capture the graphs of every batch bucket once
+    warm = {nm: np.linspace(0, 1e-3, min(n_max, 4 * args.serve_batch)) for nm in specs}
+    srv.run(warm, {nm: ys[nm][:len(warm[nm])] for nm in specs})
+    out = []
+    for rate in rates:
+        n_each = int(rate * args.serve_seconds / 2)
+        arr = {nm: serving.poisson_arrivals(rate / 2, n_each, seed=100 + i) for i, nm in enumerate(specs)}
+        res = srv.run(arr, {nm: ys[nm][:n_each] for nm in specs})
+        p = res.percentiles((50, 99))
+        fer = {nm: float(np.mean(np.any(res.cw[nm] != synth.pack_bits(pools[nm].cw[:n_each]), axis=1))) for nm in specs}
+        out.append({"offered_frames_per_s": rate, "served_frames_per_s": res.served / res.wall_s,
+                    "p50_ms": p["p50"] * 1e3, "p99_ms": p["p99"] * 1e3, "frames": res.served,
+                    "dispatches": res.dispatches, "mean_batch": float(np.mean(res.batch_sizes)), "fer": fer})
+    line = {"metric": METRIC + " (serving)", "value": max(o["served_frames_per_s"] for o in out), "unit": "frames/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "bf16x2+f64", "data": "synthetic",
+            "config": {"workload": "serving: Poisson arrivals, 50/50 RM(2,6)+CRC-6 (L=8,T=4) / RM(2,7)+CRC-6 (L=16,T=6), "
+                                   "Eb/N0 U[0.5,3] dB", "max_batch": args.serve_batch, "slots_per_code": {nm: len(v) for nm, v in srv.slots.items()},
+                       "max_wait_us": args.serve_wait_us, "seconds_per_rate": args.serve_seconds},
+            "rates": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rm26_crc6_1db")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving"], default="rm26_crc6_1db")
     ap.add_argument("--mode", choices=["bf16x2", "fp32"], default="bf16x2")
     ap.add_argument("--frames", type=int, default=0, help="override frames per step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample size in CPU seconds")
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--rates", default="1,2,5,10,20", help="serving: offered M frames/s")
+    ap.add_argument("--serve-seconds", type=float, default=0.1, help="serving: seconds of traffic per rate")
+    ap.add_argument("--serve-batch", type=int, default=65536)
+    ap.add_argument("--serve-wait-us", type=float, default=200.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
+    if args.workload == "serving":
+        run_serving(args)
+        return
     wl_cfg = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl_cfg)

@@ -82,7 +82,11 @@ typedef struct mpwsd_opts {
     int score_mode;  /* MPWSD_SCORE_BF16X2 (default) or MPWSD_SCORE_FP32 */
     int stage1_rule; /* MPWSD_RULE_TOP1 (default) or MPWSD_RULE_ANY */
     int always_on;   /* nonzero: run stage 2 on every frame, CRC or not (always-on mode, Sec. III-C) */
-    int reserved[5]; /* must be zero */
+    int use_graph;   /* nonzero: replay the decode's launch sequence as a CUDA graph. The first call with a
+                        given (workspace, buffers, B, L, T, options) captures it (on a private stream,
+                        without running it) and later identical calls replay it; the handle keeps up to
+                        256 graphs. Same results as without. */
+    int reserved[4]; /* must be zero */
 } mpwsd_opts;
 
 /* Counters accumulated on the device by every decode of a code handle since

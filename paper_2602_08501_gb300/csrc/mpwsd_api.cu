@@ -85,6 +85,23 @@ struct mpwsd_code {
     };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
+    // CUDA graphs of decode launch sequences (opts.use_graph)
+    struct GraphKey {
+        const void *ws, *y, *cw, *fl;
+        int64_t ws_B, B;  // workspace layout (base, max_B, max_L) and the call
+        int ws_L, L, T, mode, rule, aom;
+        bool operator==(const GraphKey &o) const {
+            return ws == o.ws && ws_B == o.ws_B && ws_L == o.ws_L && y == o.y && cw == o.cw && fl == o.fl &&
+                   B == o.B && L == o.L && T == o.T && mode == o.mode && rule == o.rule && aom == o.aom;
+        }
+    };
+    struct GraphEnt {
+        GraphKey key;
+        cudaGraphExec_t exec;
+        int kernels;
+    };
+    std::vector<GraphEnt> graphs;
+    cudaStream_t capture_stream = nullptr;
 };
 
 namespace {
@@ -102,8 +119,11 @@ cudaEvent_t pool_event(mpwsd_code *c) {
 
 // Launch through `fn`, counting it and, while profiling, bracketing it with
 // CUDA events on the launch stream.
+thread_local bool t_capturing = false;  // this thread is recording a decode into a graph
+
 template <class Fn>
 cudaError_t timed_launch(mpwsd_code *c, int kind, cudaStream_t s, Fn &&fn) {
+    if (t_capturing) return fn();  // counted per replay instead
     c->launches++;
     if (!c->profiling) return fn();
     std::lock_guard<std::mutex> lk(c->prof_mu);
@@ -427,6 +447,8 @@ extern "C" void mpwsd_free_code(mpwsd_code *code) {
         cudaEventDestroy(r.stop);
     }
     for (auto e : code->pool) cudaEventDestroy(e);
+    for (auto &g : code->graphs) cudaGraphExecDestroy(g.exec);
+    if (code->capture_stream) cudaStreamDestroy(code->capture_stream);
     mpwsd_workspace_free(code->default_ws);
     free_code_device(code->d);
     delete code;
@@ -442,7 +464,7 @@ static int check_opts(const mpwsd_opts *opts, mpwsd_opts *o) {
         return fail(MPWSD_EINVAL, "score_mode = %d", o->score_mode);
     if (o->stage1_rule != MPWSD_RULE_TOP1 && o->stage1_rule != MPWSD_RULE_ANY)
         return fail(MPWSD_EINVAL, "stage1_rule = %d", o->stage1_rule);
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
         if (o->reserved[i]) return fail(MPWSD_EINVAL, "reserved option fields must be zero");
     return MPWSD_OK;
 }
@@ -501,6 +523,60 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
     return MPWSD_OK;
 }
 
+// Decode through a cached CUDA graph of the launch sequence: on a miss the
+// sequence is captured on the handle's private stream (nothing runs) and
+// instantiated; every call then launches the graph on the caller's stream.
+static int decode_graph(mpwsd_code *code, Workspace &ws, const float *y_dev, int64_t B, int L, int T,
+                        const mpwsd_opts &o, uint64_t *cw_dev, uint16_t *flags_dev, cudaStream_t s) {
+    mpwsd_code::GraphKey key{ws.base,  y_dev, cw_dev, flags_dev,     ws.max_B,      B,
+                             ws.max_L, L,     T,      o.score_mode, o.stage1_rule, o.always_on};
+    std::lock_guard<std::mutex> lk(code->mu);
+    for (auto &g : code->graphs)
+        if (g.key == key) {
+            cudaError_t e = cudaGraphLaunch(g.exec, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+            code->launches += g.kernels;
+            return MPWSD_OK;
+        }
+    cudaError_t e = cudaSuccess;
+    if (!code->capture_stream) e = cudaStreamCreateWithFlags(&code->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "creating the capture stream");
+    e = cudaStreamBeginCapture(code->capture_stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    t_capturing = true;
+    int st = decode_impl(code, ws, y_dev, B, L, T, o, cw_dev, flags_dev, code->capture_stream);
+    t_capturing = false;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(code->capture_stream, &graph);
+    if (st) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    size_t nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nodes);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    if (code->graphs.size() >= 256) {
+        cudaGraphExecDestroy(code->graphs.front().exec);
+        code->graphs.erase(code->graphs.begin());
+    }
+    const int kernels = (int)nodes - 1;  // every node but the counter reset is a kernel
+    code->graphs.push_back({key, exec, kernels});
+    e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    code->launches += kernels;
+    return MPWSD_OK;
+}
+
+static int run_decode(mpwsd_code *code, Workspace &ws, const float *y_dev, int64_t B, int L, int T,
+                      const mpwsd_opts &o, uint64_t *cw_dev, uint16_t *flags_dev, cudaStream_t s) {
+    if (o.use_graph && !code->profiling) return decode_graph(code, ws, y_dev, B, L, T, o, cw_dev, flags_dev, s);
+    return decode_impl(code, ws, y_dev, B, L, T, o, cw_dev, flags_dev, s);
+}
+
 static int check_decode_args(mpwsd_code *code, const float *y_dev, int64_t B, int L, int T, const mpwsd_opts *opts,
                              uint64_t *cw_dev, uint16_t *flags_dev, mpwsd_opts *o) {
     if (!code) return fail(MPWSD_EINVAL, "code is NULL");
@@ -526,7 +602,7 @@ extern "C" int mpwsd_decode_ws(mpwsd_code *code, mpwsd_workspace *ws, const floa
         return fail(MPWSD_EINVAL, "B = %lld, L = %d exceed the workspace (%lld, %d)", (long long)B, L,
                     (long long)ws->w.max_B, ws->w.max_L);
     if (B == 0) return MPWSD_OK;
-    return decode_impl(code, ws->w, y_dev, B, L, T, o, cw_dev, flags_dev, (cudaStream_t)stream);
+    return run_decode(code, ws->w, y_dev, B, L, T, o, cw_dev, flags_dev, (cudaStream_t)stream);
 }
 
 extern "C" int mpwsd_decode(mpwsd_code *code, const float *y_dev, int64_t B, int L, int T, const mpwsd_opts *opts,
@@ -535,18 +611,29 @@ extern "C" int mpwsd_decode(mpwsd_code *code, const float *y_dev, int64_t B, int
     int st = check_decode_args(code, y_dev, B, L, T, opts, cw_dev, flags_dev, &o);
     if (st) return st;
     if (B == 0) return MPWSD_OK;
-    std::lock_guard<std::mutex> lk(code->mu);
-    mpwsd_workspace *ws = code->default_ws;
-    if (!ws || ws->w.max_B < B || ws->w.max_L < L) {
-        const int64_t nb = std::max<int64_t>(B, ws ? ws->w.max_B : 0);
-        const int nl = std::max(L, ws ? ws->w.max_L : 0);
-        mpwsd_workspace *nw = nullptr;
-        st = mpwsd_workspace_create(code, nb, nl, &nw);
-        if (st) return st;
-        mpwsd_workspace_free(ws);
-        code->default_ws = ws = nw;
+    mpwsd_workspace *ws;
+    {
+        std::lock_guard<std::mutex> lk(code->mu);
+        ws = code->default_ws;
+        if (!ws || ws->w.max_B < B || ws->w.max_L < L) {
+            const int64_t nb = std::max<int64_t>(B, ws ? ws->w.max_B : 0);
+            const int nl = std::max(L, ws ? ws->w.max_L : 0);
+            mpwsd_workspace *nw = nullptr;
+            st = mpwsd_workspace_create(code, nb, nl, &nw);
+            if (st) return st;
+            // graphs recorded on the old workspace go with it
+            for (auto it = code->graphs.begin(); it != code->graphs.end();)
+                if (ws && it->key.ws == ws->w.base) {
+                    cudaGraphExecDestroy(it->exec);
+                    it = code->graphs.erase(it);
+                } else {
+                    ++it;
+                }
+            mpwsd_workspace_free(ws);
+            code->default_ws = ws = nw;
+        }
     }
-    return decode_impl(code, ws->w, y_dev, B, L, T, o, cw_dev, flags_dev, (cudaStream_t)stream);
+    return run_decode(code, ws->w, y_dev, B, L, T, o, cw_dev, flags_dev, (cudaStream_t)stream);
 }
 
 extern "C" int mpwsd_stage1_list(mpwsd_code *code, const float *y_dev, int64_t B, int L, uint64_t *list_cw_dev,

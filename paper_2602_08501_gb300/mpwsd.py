@@ -37,7 +37,7 @@ class MpwsdError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("score_mode", ctypes.c_int), ("stage1_rule", ctypes.c_int), ("always_on", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class _KTime(ctypes.Structure):
@@ -202,15 +202,16 @@ class Code:
             pass
 
     @staticmethod
-    def _opts(score_mode, rule, always_on):
+    def _opts(score_mode, rule, always_on, use_graph=False):
         o = _Opts()
         o.score_mode = {"bf16x2": SCORE_BF16X2, "fp32": SCORE_FP32}.get(score_mode, score_mode)
         o.stage1_rule = {"top1": RULE_TOP1, "any": RULE_ANY}.get(rule, rule)
         o.always_on = int(bool(always_on))
+        o.use_graph = int(bool(use_graph))
         return o
 
     def decode(self, y, L: int, T: int, score_mode="bf16x2", rule="top1", always_on=False, cw_out=None,
-               flags_out=None, stream=None, workspace: Workspace | None = None):
+               flags_out=None, stream=None, workspace: Workspace | None = None, use_graph: bool = False):
         """Two-stage decode of y (B x n float32 CUDA tensor). Returns (cw, flags)
         as CUDA tensors (B x W int64 bit patterns, B int16); asynchronous."""
         import torch
@@ -222,7 +223,7 @@ class Code:
             cw_out = torch.empty((B, self.W), dtype=torch.int64, device=y.device)
         if flags_out is None:
             flags_out = torch.empty((B,), dtype=torch.int16, device=y.device)
-        o = self._opts(score_mode, rule, always_on)
+        o = self._opts(score_mode, rule, always_on, use_graph)
         args = (_dev(y, torch.float32, "y"), B, int(L), int(T), ctypes.byref(o), _dev(cw_out, torch.int64, "cw_out"),
                 _dev(flags_out, torch.int16, "flags_out"), _stream_ptr(stream))
         if workspace is None:

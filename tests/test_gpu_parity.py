@@ -203,3 +203,28 @@ def test_stats_counters(mp, rm26, rm26_or):
     assert st["trajectories"] == 8 * st["stage2_frames"]
     assert st["pattern_evals"] == int(ref["evals"].sum())
     assert st["kernel_launches"] >= 1 + 2 * 4 + 1  # stage 1, T x (score + re-rank, rescan), final
+
+
+def test_graph_replay_matches_direct_launches(mp, rm26):
+    """use_graph: the first call records the launch sequence, later identical
+    calls replay it; results equal the direct launches, call after call."""
+    wl = synth.make_workload("rm26_crc6", 1.0, 3000, seed=41)
+    y = _dev(wl.y)
+    ws = rm26.workspace(4096, 8)
+    cw_ref, fl_ref = rm26.decode(y, 8, 4, workspace=ws)
+    cw = torch.empty_like(cw_ref)
+    fl = torch.empty_like(fl_ref)
+    for mode in ("bf16x2", "fp32"):
+        ref = rm26.decode(y, 8, 4, score_mode=mode, workspace=ws)
+        for _ in range(3):
+            cw.fill_(-1)
+            fl.fill_(-1)
+            rm26.decode(y, 8, 4, score_mode=mode, workspace=ws, cw_out=cw, flags_out=fl, use_graph=True)
+            torch.cuda.synchronize()
+            assert torch.equal(cw, ref[0]) and torch.equal(fl, ref[1])
+    # new input data in the same buffer: the replay reads it
+    y.copy_(_dev(synth.make_workload("rm26_crc6", 2.0, 3000, seed=42).y))
+    ref = rm26.decode(y, 8, 4, workspace=ws)
+    rm26.decode(y, 8, 4, workspace=ws, cw_out=cw, flags_out=fl, use_graph=True)
+    torch.cuda.synchronize()
+    assert torch.equal(cw, ref[0]) and torch.equal(fl, ref[1])

@@ -1,0 +1,61 @@
+"""The continuous-batching request loop (serving.py) on a mixed two-code
+Poisson stream: every frame is served, each result is the same as when the
+frame is decoded in one big batch and when it is decoded alone, and a memory
+budget that cannot hold every slot refuses the extra slots but still serves."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_common import cuda_or_skip, to_words, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(mp, n_each, rate, seed):
+    from paper_2602_08501_gb300 import serving
+
+    specs = {"rm26": serving.CodeSpec(mp.Code.rm(6, 2, crc_poly=0x21, crc_len=6, weights=[16]), 8, 4),
+             "rm27": serving.CodeSpec(mp.Code.rm(7, 2, crc_poly=0x21, crc_len=6, weights=[32]), 16, 6)}
+    wls = {"rm26": synth.make_workload("rm26_crc6", (0.5, 3.0), n_each, seed=seed),
+           "rm27": synth.make_workload("rm27_crc6", (0.5, 3.0), n_each, seed=seed + 1)}
+    arrivals = {nm: serving.poisson_arrivals(rate / 2, n_each, seed=seed + 10 + i) for i, nm in enumerate(specs)}
+    ys = {nm: torch.from_numpy(wls[nm].y).pin_memory() for nm in specs}
+    return serving, specs, wls, arrivals, ys
+
+
+def test_serving_results_equal_alone_and_in_one_batch():
+    mp = cuda_or_skip()
+    serving, specs, wls, arrivals, ys = _setup(mp, 6000, 2e6, seed=50)
+    srv = serving.Server(specs, max_batch=4096, slots_per_code=2, min_batch=512, max_wait_s=100e-6)
+    res = srv.run(arrivals, ys)
+    assert res.served == 12000 and res.dispatches >= 4
+    for nm, sp in specs.items():
+        assert np.all(np.isfinite(res.latency_s[nm])) and np.all(res.latency_s[nm] >= 0)
+        y = wls[nm].y
+        cw, fl = sp.code.decode(torch.from_numpy(y).cuda(), sp.L, sp.T)
+        torch.cuda.synchronize()
+        assert np.array_equal(res.cw[nm], to_words(cw)), nm
+        assert np.array_equal(res.flags[nm], fl.cpu().numpy().view(np.uint16)), nm
+        rng = np.random.default_rng(1)
+        for f in rng.choice(y.shape[0], 60, replace=False):
+            c1, f1 = sp.code.decode(torch.from_numpy(y[f:f + 1]).cuda(), sp.L, sp.T)
+            torch.cuda.synchronize()
+            assert np.array_equal(res.cw[nm][f], to_words(c1)[0]) and res.flags[nm][f] == f1.cpu().numpy().view(np.uint16)[0]
+    p = res.percentiles()
+    assert p["p50"] <= p["p99"] < 1.0
+
+
+def test_serving_admission_by_memory():
+    mp = cuda_or_skip()
+    serving, specs, wls, arrivals, ys = _setup(mp, 3000, 1e6, seed=60)
+    # room for about one slot per code
+    one = {nm: sp.code.workspace_bytes(2048, sp.L) + 2048 * (sp.code.n * 4 + sp.code.W * 8 + 2) for nm, sp in specs.items()}
+    srv = serving.Server(specs, max_batch=2048, slots_per_code=3, mem_budget_bytes=sum(one.values()) + 1024,
+                         min_batch=256, max_wait_s=100e-6)
+    assert {nm: len(v) for nm, v in srv.slots.items()} == {"rm26": 1, "rm27": 1} and sum(srv.refused.values()) == 4
+    res = srv.run(arrivals, ys)
+    assert res.served == 6000 and sum(res.refused_slots.values()) > 0
+    for nm, sp in specs.items():
+        cw, fl = sp.code.decode(torch.from_numpy(wls[nm].y).cuda(), sp.L, sp.T)
+        torch.cuda.synchronize()
+        assert np.array_equal(res.cw[nm], to_words(cw))
