@@ -456,11 +456,16 @@ def run_serving(args):
     pools = {"rm26": synth.make_workload("rm26_crc6", (0.5, 3.0), n_max, seed=4),
              "rm27": synth.make_workload("rm27_crc6", (0.5, 3.0), n_max, seed=5)}
     ys = {nm: torch.from_numpy(pools[nm].y).pin_memory() for nm in specs}
+    from paper_2602_08501_gb300 import autotune
+
+    tuned = {}
+    for nm, sp in specs.items():  # choose the pattern-split target on a sample of each code's frames
+        sample = ys[nm][:min(n_max, 32768)].cuda()
+        sizes = [b for b in (256, 4096, 32768) if b <= sample.shape[0]]
+        tuned[nm] = autotune.tune(sp.code, sample, sp.L, sp.T, batch_sizes=sizes, reps=5)
     srv = serving.Server(specs, max_batch=args.serve_batch, slots_per_code=4, min_batch=args.serve_batch // 8,
                          max_wait_s=args.serve_wait_us * 1e-6)
-    # warm-up: capture the graphs of every batch bucket once
-    warm = {nm: np.linspace(0, 1e-3, min(n_max, 4 * args.serve_batch)) for nm in specs}
-    srv.run(warm, {nm: ys[nm][:len(warm[nm])] for nm in specs})
+    srv.warmup()  # records the decode graph of every batch bucket on every slot
     out = []
     for rate in rates:
         n_each = int(rate * args.serve_seconds / 2)
@@ -475,7 +480,8 @@ def run_serving(args):
             "n_gpus": 1, "higher_is_better": True, "dtype": "bf16x2+f64", "data": "synthetic",
             "config": {"workload": "serving: Poisson arrivals, 50/50 RM(2,6)+CRC-6 (L=8,T=4) / RM(2,7)+CRC-6 (L=16,T=6), "
                                    "Eb/N0 U[0.5,3] dB", "max_batch": args.serve_batch, "slots_per_code": {nm: len(v) for nm, v in srv.slots.items()},
-                       "max_wait_us": args.serve_wait_us, "seconds_per_rate": args.serve_seconds},
+                       "max_wait_us": args.serve_wait_us, "seconds_per_rate": args.serve_seconds,
+                       "tuned_split_items": {nm: t["value"] for nm, t in tuned.items()}},
             "rates": out}
     print(json.dumps(line), flush=True)
 

@@ -275,6 +275,18 @@ typedef struct mpwsd_kernel_time {
 MPWSD_API int mpwsd_profile_begin(mpwsd_code *code);
 MPWSD_API int mpwsd_profile_end(mpwsd_code *code, mpwsd_kernel_time *out);
 
+/* Tunable launch parameters of a code handle (set by the autotuner in
+ * paper_2602_08501_gb300/autotune.py or by hand; they change speed only, never
+ * results). */
+#define MPWSD_TUNE_SPLIT_ITEMS 0 /* tensor-core scoring: when a launch has fewer 256-row units than this, each
+                                    unit's pattern tiles are split into chunks scanned by different CTAs so the
+                                    launch has about this many work items; 0 = never split. Default: SMs / 2 */
+#define MPWSD_TUNE_KNOBS 1
+
+/* Set / get a tunable (MPWSD_EINVAL for an unknown knob or a negative value). */
+MPWSD_API int mpwsd_tune_set(mpwsd_code *code, int knob, int value);
+MPWSD_API int mpwsd_tune_get(const mpwsd_code *code, int knob, int *value);
+
 /* Read (synchronising the device) / reset the handle's counters. */
 MPWSD_API int mpwsd_stats_get(mpwsd_code *code, mpwsd_stats *out);
 MPWSD_API int mpwsd_stats_reset(mpwsd_code *code);

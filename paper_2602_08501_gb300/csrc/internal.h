@@ -53,7 +53,14 @@ struct Workspace {
     int *rescan_rows = nullptr;   // rows whose top-K overflowed the margin
     float *topk_val = nullptr;    // F*L x K
     int *topk_idx = nullptr;      // F*L x K
+    // pattern-split of the tensor-core scoring kernel (absent: no split)
+    float *split_val = nullptr;   // kSplitItemsPerSm * num_sms items x 256 rows x K partial lists
+    int *split_idx = nullptr;
+    int *unit_done = nullptr;     // per 256-row unit: chunks finished in the current launch
 };
+
+// Work items of the split: at most this many per SM (units x chunks < 4 x SMs).
+constexpr int kSplitItemsPerSm = 4;
 
 // Everything the kernels need to know about a loaded code.
 struct CodeDev {
@@ -79,6 +86,7 @@ struct CodeDev {
     // no copies, so its consumers' waits run out on purpose.
     unsigned long long wait_limit_ns = 2000000000ull;
     int test_stall = 0;
+    int split_items = 0;  // MPWSD_TUNE_SPLIT_ITEMS (0: no pattern split)
 };
 
 struct SclArgs {
@@ -114,6 +122,11 @@ struct ScoreArgs {
     int fused;
     int iter;
     Workspace ws;
+    // split buffers (both modes; nullptr: every CTA scans whole units)
+    float *split_val;
+    int *split_idx;
+    int *unit_done;
+    int split_items;  // target work items of the split (<= kSplitItemsPerSm / 2 x SMs)
 };
 
 // Launchers (return cudaError_t of the launch).

@@ -55,6 +55,7 @@ cudaError_t dev_alloc(void **p, size_t bytes) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+
 // Row i of [[1,0],[1,1]]^{(x)m} has ones exactly at the submasks j of i.
 inline bool kron_entry(int i, int j) { return (i & j) == j; }
 
@@ -262,6 +263,7 @@ extern "C" int mpwsd_load_code(int n, const uint8_t *G, const uint8_t *frozen, i
         delete c;
         return cuda_fail(e, "cudaDeviceGetAttribute");
     }
+    d.split_items = d.num_sms / 2;
 
     // host images
     std::vector<uint32_t> supp((size_t)n_patterns * d.wq_max, 0);
@@ -417,17 +419,31 @@ extern "C" int mpwsd_workspace_create(const mpwsd_code *code, int64_t max_B, int
     if (st) return st;
     mpwsd_workspace *ws = new (std::nothrow) mpwsd_workspace();
     if (!ws) return fail(MPWSD_ENOMEM, "host allocation");
-    cudaError_t e = dev_alloc(&ws->w.base, bytes);
+    // tail: buffers of the pattern split of the tensor-core scoring kernel
+    const size_t split_items = (size_t)kSplitItemsPerSm * std::max(code->d.num_sms, 1);
+    const size_t split_entries = split_items * 256 * kTopK;
+    const size_t split_bytes = align256(split_entries * 4) * 2 + align256(split_items * sizeof(int));
+    cudaError_t e = dev_alloc(&ws->w.base, bytes + split_bytes);
     if (e != cudaSuccess) {
         delete ws;
         cudaGetLastError();  // clear the sticky-free allocation error
         return cuda_fail(e, "workspace allocation");
     }
-    ws->w.bytes = bytes;
+    ws->w.bytes = bytes + split_bytes;
     ws->w.max_B = max_B;
     ws->w.max_L = max_L;
     cudaGetDevice(&ws->w.device);
     ws_layout(code->d, max_B, max_L, &ws->w);
+    char *tail = (char *)ws->w.base + bytes;
+    ws->w.split_val = (float *)tail;
+    ws->w.split_idx = (int *)(tail + align256(split_entries * 4));
+    ws->w.unit_done = (int *)(tail + 2 * align256(split_entries * 4));
+    e = cudaMemset(ws->w.unit_done, 0, split_items * sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(ws->w.base);
+        delete ws;
+        return cuda_fail(e, "workspace initialisation");
+    }
     *out = ws;
     return MPWSD_OK;
 }
@@ -513,6 +529,10 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
         a.fused = 1;  // the scoring kernel re-ranks, hops and compacts each row itself
         a.iter = it;
         a.ws = ws;
+        a.split_val = ws.split_val;
+        a.split_idx = ws.split_idx;
+        a.unit_done = ws.unit_done;
+        a.split_items = d.split_items;
         e = launch_score(code, o.score_mode, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "scoring launch");
         e = timed_launch(code, MPWSD_KERNEL_RESCAN, s, [&] { return launch_rescan(d, ws, it, L, y_dev, s); });
@@ -746,6 +766,26 @@ extern "C" int mpwsd_profile_end(mpwsd_code *code, mpwsd_kernel_time *out) {
     }
     code->recs.clear();
     return status;
+}
+
+extern "C" int mpwsd_tune_set(mpwsd_code *code, int knob, int value) {
+    if (!code) return fail(MPWSD_EINVAL, "code is NULL");
+    if (knob != MPWSD_TUNE_SPLIT_ITEMS) return fail(MPWSD_EINVAL, "unknown knob %d", knob);
+    // units x chunks stays below kSplitItemsPerSm x SMs, the size of the split buffers
+    const int cap = kSplitItemsPerSm / 2 * code->d.num_sms;
+    if (value < 0 || value > cap) return fail(MPWSD_EINVAL, "split items %d outside 0..%d", value, cap);
+    std::lock_guard<std::mutex> lk(code->mu);
+    code->d.split_items = value;
+    for (auto &g : code->graphs) cudaGraphExecDestroy(g.exec);  // recorded with the old value
+    code->graphs.clear();
+    return MPWSD_OK;
+}
+
+extern "C" int mpwsd_tune_get(const mpwsd_code *code, int knob, int *value) {
+    if (!code || !value) return fail(MPWSD_EINVAL, "NULL argument");
+    if (knob != MPWSD_TUNE_SPLIT_ITEMS) return fail(MPWSD_EINVAL, "unknown knob %d", knob);
+    *value = code->d.split_items;
+    return MPWSD_OK;
 }
 
 extern "C" int mpwsd_stats_reset(mpwsd_code *code) {

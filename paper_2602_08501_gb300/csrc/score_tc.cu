@@ -38,6 +38,7 @@
 namespace mpwsd {
 namespace {
 
+static_assert(kTopK == 4, "the split merge loads one float4 / int4 per chunk list");
 constexpr int BM = 128;                 // rows per MMA (TMEM lanes)
 constexpr int RB = 2;                   // row blocks per unit, sharing every pattern tile
 constexpr int UM = BM * RB;             // rows per unit
@@ -229,6 +230,8 @@ struct TcShared {
     uint64_t *b_full, *b_empty, *a_full, *a_empty, *acc_full, *acc_empty;
     uint32_t *tmem_slot;
     int *abort_flag;
+    int *last_flag;
+    uint64_t *epi_pub, *epi_last;  // split: chunk lists published / last-chunk flag ready
 };
 
 __device__ __forceinline__ void record_abort(const TcShared &sh, const CodeDev &c) {
@@ -253,17 +256,26 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
     sh.a_empty = sh.a_full + C::A_BUFS;
     sh.acc_full = sh.a_empty + C::A_BUFS;
     sh.acc_empty = sh.acc_full + 2;
-    sh.tmem_slot = (uint32_t *)(sh.acc_empty + 2);
+    sh.epi_pub = sh.acc_empty + 2;
+    sh.epi_last = sh.epi_pub + 1;
+    sh.tmem_slot = (uint32_t *)(sh.epi_last + 1);
     sh.abort_flag = (int *)(sh.tmem_slot + 1);
+    sh.last_flag = sh.abort_flag + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nrows = a.n_rows_dev ? *a.n_rows_dev : (int)a.n_rows;
     const int nunits = (nrows + UM - 1) / UM;
-    const int my_units =
-        nunits > (int)blockIdx.x ? (nunits - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
-    if (my_units == 0) return;
     const int P = (int)c.P;
     const int nt = (P + BN - 1) / BN;
+    // Work items: (unit, chunk of pattern tiles). When there are fewer units than
+    // the split target, each unit's tiles are split into nch chunks scanned by
+    // different CTAs; the last CTA to finish a unit merges the chunks' lists.
+    int nch = 1;
+    if (a.split_val && nunits < a.split_items) nch = min(nt, (a.split_items + nunits - 1) / nunits);
+    const int nitems = nunits * nch;
+    const int my_units =
+        nitems > (int)blockIdx.x ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    if (my_units == 0) return;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::B_STAGES; ++s) {
@@ -278,6 +290,8 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
             mbar_init(smem_u32(&sh.acc_full[s]), 1);
             mbar_init(smem_u32(&sh.acc_empty[s]), kEpiThreads);
         }
+        mbar_init(smem_u32(sh.epi_pub), kEpiThreads);
+        mbar_init(smem_u32(sh.epi_last), 1);
         *sh.abort_flag = 0;
         fence_mbar_init();
     }
@@ -299,7 +313,8 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
             int g = 0;
             bool ok = true;
             for (int i = 0; i < my_units && ok; ++i) {
-                for (int j = 0; j < nt; ++j, ++g) {
+                const int item = (int)blockIdx.x + i * (int)gridDim.x, ch = item % nch;
+                for (int j = ch * nt / nch; j < (ch + 1) * nt / nch; ++j, ++g) {
                     const int s = g % C::B_STAGES;
                     const uint32_t ph = (uint32_t)(g / C::B_STAGES) & 1u;
                     if (!mbar_wait(smem_u32(&sh.b_empty[s]), ph ^ 1u, abort_flag, c.wait_limit_ns)) {
@@ -338,7 +353,8 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                 }
                 tc_fence_after();
                 const uint32_t abuf = smem_u32(Abase + ab * C::A_BUF_BYTES);
-                for (int j = 0; j < nt; ++j, ++gb, ++gacc) {
+                const int item = (int)blockIdx.x + i * (int)gridDim.x, ch = item % nch;
+                for (int j = ch * nt / nch; j < (ch + 1) * nt / nch; ++j, ++gb, ++gacc) {
                     const int s = gb % C::B_STAGES;
                     if (!mbar_wait(smem_u32(&sh.b_full[s]), (uint32_t)(gb / C::B_STAGES) & 1u, abort_flag,
                                    c.wait_limit_ns)) {
@@ -399,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                 if (lane == 0) record_abort(sh, c);
                 break;
             }
-            const int unit = (int)blockIdx.x + i * (int)gridDim.x;
+            const int unit = ((int)blockIdx.x + i * (int)gridDim.x) / nch;
             const int row0 = unit * UM + rb * BM;
             // each lane gathers the frame and centre of 4 rows at once
             int fr[4];
@@ -494,8 +510,10 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
         int gacc = 0;
         bool ok = true;
         unsigned long long my_cand = 0, my_hops = 0;
+        int nsplit = 0;  // split items finished by this CTA (phase of epi_pub / epi_last)
         for (int i = 0; i < my_units && ok; ++i) {
-            const int unit = (int)blockIdx.x + i * (int)gridDim.x;
+            const int item = (int)blockIdx.x + i * (int)gridDim.x;
+            const int unit = item / nch, ch = item % nch;
             const int row = unit * UM + rb * BM + r;
             float tv[kTopK];
             int ti[kTopK];
@@ -519,7 +537,7 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                 eps2 = __fmul_ru(2.0f * kEpsScale, __fmul_ru(l1, 1.0f + 1.0f / 1024.0f));
             }
             float thr = CUDART_INF_F;
-            for (int j = 0; j < nt; ++j, ++gacc) {
+            for (int j = ch * nt / nch; j < (ch + 1) * nt / nch; ++j, ++gacc) {
                 const int acc = gacc & 1;
                 bool w = mbar_wait(smem_u32(&sh.acc_full[acc]), (uint32_t)(gacc >> 1) & 1u, abort_flag, c.wait_limit_ns);
                 w = __all_sync(0xffffffffu, w);
@@ -549,6 +567,68 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                 mbar_arrive(smem_u32(&sh.acc_empty[acc]));
             }
             if (!ok) break;
+            if (nch > 1) {
+                // publish this chunk's list; the last chunk of the unit merges them all
+                const size_t slot = ((size_t)item * UM + rb * BM + r) * kTopK;
+#pragma unroll
+                for (int k = 0; k < kTopK; ++k) {
+                    a.split_val[slot + k] = tv[k];
+                    a.split_idx[slot + k] = ti[k];
+                }
+                __threadfence();
+                // all epilogue threads published -> one thread counts the chunk -> all read
+                // whether it was the unit's last (bounded waits, so an abort cannot wedge them)
+                const uint32_t par = (uint32_t)(nsplit & 1);
+                ++nsplit;
+                mbar_arrive(smem_u32(sh.epi_pub));
+                if (threadIdx.x == 4 * 32) {
+                    if (mbar_wait(smem_u32(sh.epi_pub), par, abort_flag, c.wait_limit_ns)) {
+                        *(volatile int *)sh.last_flag = (atomicAdd(&a.unit_done[unit], 1) == nch - 1);
+                        __threadfence();
+                    }
+                    mbar_arrive(smem_u32(sh.epi_last));
+                }
+                bool w2 = mbar_wait(smem_u32(sh.epi_last), par, abort_flag, c.wait_limit_ns);
+                w2 = __all_sync(0xffffffffu, w2);
+                if (!w2) {
+                    ok = false;
+                    break;
+                }
+                const bool last = *(volatile int *)sh.last_flag != 0;
+                if (!last) continue;
+                __threadfence();
+#pragma unroll
+                for (int k = 0; k < kTopK; ++k) {
+                    tv[k] = CUDART_INF_F;
+                    ti[k] = -1;
+                }
+                thr = CUDART_INF_F;
+                // chunks in pattern order (ties keep the lower index), four chunks' loads in flight
+                for (int c0 = 0; c0 < nch; c0 += 4) {
+                    float pv[4][kTopK];
+                    int pi[4][kTopK];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const size_t src = ((size_t)(unit * nch + min(c0 + u, nch - 1)) * UM + rb * BM + r) * kTopK;
+                        const float4 v4 = __ldcg(reinterpret_cast<const float4 *>(a.split_val + src));
+                        const int4 i4 = __ldcg(reinterpret_cast<const int4 *>(a.split_idx + src));
+                        pv[u][0] = v4.x; pv[u][1] = v4.y; pv[u][2] = v4.z; pv[u][3] = v4.w;
+                        pi[u][0] = i4.x; pi[u][1] = i4.y; pi[u][2] = i4.z; pi[u][3] = i4.w;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (c0 + u >= nch) break;
+#pragma unroll
+                        for (int k = 0; k < kTopK; ++k) {
+                            if (pi[u][k] >= 0 && pv[u][k] < thr) {
+                                topk_insert<kTopK>(tv, ti, pv[u][k], pi[u][k]);
+                                thr = admit_thr(tv, eps2);
+                            }
+                        }
+                    }
+                }
+                if (threadIdx.x == 4 * 32) a.unit_done[unit] = 0;  // ready for the next launch
+            }
             if (a.fused) {
                 // finish the row: FP64 re-rank of the kept candidates and the hop (Algorithm 1)
                 int outcome = kRowNone, t = 0;

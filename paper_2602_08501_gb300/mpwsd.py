@@ -24,6 +24,7 @@ RULE_TOP1, RULE_ANY = 0, 1
 FLAG_STAGE2, FLAG_CRC_OK, FLAG_RESCAN, FLAG_ERROR = 0x1, 0x2, 0x4, 0x100
 ITERS_SHIFT = 4
 MAX_L, MAX_T, TOPK = 32, 15, 4
+TUNE_SPLIT_ITEMS = 0
 
 _lock = threading.Lock()
 _lib = None
@@ -86,6 +87,8 @@ def lib():
             "mpwsd_stats_get": (i32, [P, ctypes.POINTER(_Stats)]),
             "mpwsd_stats_reset": (i32, [P]),
             "mpwsd_enumerate_codewords": (i32, [i32, P, P, i32, P, i64, ctypes.POINTER(ctypes.c_int64)]),
+            "mpwsd_tune_set": (i32, [P, i32, i32]),
+            "mpwsd_tune_get": (i32, [P, i32, ctypes.POINTER(ctypes.c_int)]),
             "mpwsd_profile_begin": (i32, [P]),
             "mpwsd_profile_end": (i32, [P, ctypes.POINTER(_KTime)]),
         }
@@ -273,6 +276,14 @@ class Code:
 
     def reset_stats(self):
         _check(lib().mpwsd_stats_reset(self._h), "stats_reset")
+
+    def tune_set(self, knob: int, value: int):
+        _check(lib().mpwsd_tune_set(self._h, int(knob), int(value)), "tune_set")
+
+    def tune_get(self, knob: int) -> int:
+        v = ctypes.c_int(0)
+        _check(lib().mpwsd_tune_get(self._h, int(knob), ctypes.byref(v)), "tune_get")
+        return int(v.value)
 
     def profile_begin(self):
         """Record CUDA events around every kernel this handle launches."""

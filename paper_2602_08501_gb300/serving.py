@@ -125,6 +125,25 @@ class Server:
                     stream=torch.cuda.Stream(), done=torch.cuda.Event(enable_timing=True)))
         self.mem_used = used
 
+    def warmup(self):
+        """Record the decode graph of every batch bucket on every slot (all-zero
+        frames), so no capture happens while requests are being served."""
+        torch = self.torch
+        for nm, slots in self.slots.items():
+            sp = self.specs[nm]
+            for s in slots:
+                b = 256
+                while True:
+                    bp = min(b, self.max_batch)
+                    with torch.cuda.stream(s.stream):
+                        s.y[:bp].zero_()
+                        sp.code.decode(s.y[:bp], sp.L, sp.T, score_mode=self.score_mode, cw_out=s.cw[:bp],
+                                       flags_out=s.fl[:bp], stream=s.stream, workspace=s.ws, use_graph=self.use_graph)
+                    if bp >= self.max_batch:
+                        break
+                    b *= 2
+        torch.cuda.synchronize()
+
     def run(self, arrivals: dict, y_pinned: dict) -> ServeResult:
         """arrivals[code]: sorted arrival times (s) of that code's frames;
         y_pinned[code]: matching pinned CPU tensor, frames in arrival order."""

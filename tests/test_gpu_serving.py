@@ -59,3 +59,24 @@ def test_serving_admission_by_memory():
         cw, fl = sp.code.decode(torch.from_numpy(wls[nm].y).cuda(), sp.L, sp.T)
         torch.cuda.synchronize()
         assert np.array_equal(res.cw[nm], to_words(cw))
+
+
+def test_autotune_picks_a_candidate_and_output_is_unchanged(tmp_path, monkeypatch):
+    mp = cuda_or_skip()
+    from paper_2602_08501_gb300 import autotune
+
+    monkeypatch.setenv("MPWSD_TUNE_CACHE", str(tmp_path / "tune.json"))
+    code = mp.Code.rm(7, 2, crc_poly=0x21, crc_len=6, weights=[32])
+    wl = synth.make_workload("rm27_crc6", 1.5, 4096, seed=70)
+    y = torch.from_numpy(wl.y).cuda()
+    outs = {}
+    for v in (0, 16, 76, 152):
+        code.tune_set(mp.TUNE_SPLIT_ITEMS, v)
+        cw, fl = code.decode(y, 16, 6)
+        torch.cuda.synchronize()
+        outs[v] = (cw.clone(), fl.clone())
+    for v in outs:
+        assert torch.equal(outs[v][0], outs[0][0]) and torch.equal(outs[v][1], outs[0][1])
+    r = autotune.tune(code, y, 16, 6, batch_sizes=(256, 4096), reps=3)
+    assert not r["cached"] and code.tune_get(mp.TUNE_SPLIT_ITEMS) == r["value"]
+    assert autotune.tune(code, y, 16, 6, batch_sizes=(256, 4096), reps=3)["cached"]
