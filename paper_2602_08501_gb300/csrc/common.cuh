@@ -40,17 +40,29 @@ __device__ __forceinline__ void topk_insert(float (&v)[K], int (&ix)[K], float s
 // are grid integers round(y 2^19) (|.| < 2^23) and at most 128 of them are
 // added, so the sum is accumulated exactly in int32 and converted once; this is
 // the same number an FP64 summation gives (exact on the grid) at a fraction of
-// the FP64-pipe work.
-__device__ __forceinline__ double exact_score(const float *yr, const uint64_t *c, const uint64_t *p, int W) {
+// the FP64-pipe work. The support list of p (4 uint8 indices per word, padded
+// with index n) is decoded 16 indices at a time, so their 16 loads of y are in
+// flight together instead of one after another.
+__device__ __forceinline__ double exact_score(const float *yr, const uint64_t *c, int W, const uint32_t *supp,
+                                              int wq, int n) {
+    const uint64_t c0 = c[0], c1 = W > 1 ? c[1] : 0ull;
     int s = 0;
-    for (int w = 0; w < W; ++w) {
-        uint64_t m = p[w];
-        const uint64_t cw = c[w];
-        while (m) {
-            const int b = __ffsll((long long)m) - 1;
-            m &= m - 1;
-            const int v = grid_q(yr[w * 64 + b]);
-            s += ((cw >> b) & 1ull) ? -v : v;
+    for (int q0 = 0; q0 < wq; q0 += 4) {
+        uint32_t wd[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) wd[u] = q0 + u < wq ? supp[q0 + u] : 0xffffffffu;
+        float v[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int j = (int)((wd[e >> 2] >> (8 * (e & 3))) & 255u);
+            v[e] = j < n ? yr[j] : 0.0f;
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int j = (int)((wd[e >> 2] >> (8 * (e & 3))) & 255u);
+            const uint64_t word = (j & 64) ? c1 : c0;
+            const int g = grid_q(v[e]);  // 0 for padding
+            s += ((word >> (j & 63)) & 1ull) ? -g : g;
         }
     }
     return (double)s * (1.0 / 524288.0);
@@ -106,7 +118,7 @@ __device__ __forceinline__ int resolve_row(const Workspace &ws, const CodeDev &c
 #pragma unroll
     for (int q = 0; q < kTopK; ++q) {
         if (ix[q] >= 0 && v[q] <= thr) {
-            const double s = exact_score(yr, cw, c.pat_bits + (int64_t)ix[q] * c.W, c.W);
+            const double s = exact_score(yr, cw, c.W, c.pat_supp + (int64_t)ix[q] * c.wq_max, c.wq_max, c.n);
             ++cand;
             if (s < best || (s == best && ix[q] < bp)) {
                 best = s;

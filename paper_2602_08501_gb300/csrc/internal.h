@@ -9,7 +9,10 @@
 namespace mpwsd {
 
 constexpr int kTopK = MPWSD_TOPK;
-constexpr int kTcPatternsPerTile = 128;  // pattern tile of the tensor-core scoring kernel
+// Pattern tile of the tensor-core scoring kernel (the MMA N): 256 patterns
+// for n = 64 (one 128 x 256 x 16 MMA chain per row block), 128 for n = 128
+// (shared memory holds fewer, twice-as-deep tiles).
+__host__ __device__ constexpr int tc_patterns_per_tile(int n) { return n == 64 ? 256 : 128; }
 constexpr int kGridShift = 19;            // y is read on the 2^-19 grid
 constexpr int kGridMax = (1 << 23) - 1;   // |round(y 2^19)| <= 2^23 - 1
 // Margin of the near-tie re-rank: every approximate score is within
@@ -75,7 +78,7 @@ struct CodeDev {
     // device arrays
     uint64_t *pat_bits = nullptr;   // P x W
     uint32_t *pat_supp = nullptr;   // P x wq_max, 4 uint8 indices per word, padded with index n
-    uint16_t *pat_tiles = nullptr;  // ceil(P/128) tiles of 128 x n bf16, smem image (128B swizzle, K-major)
+    uint16_t *pat_tiles = nullptr;  // tiles of tc_patterns_per_tile(n) x n bf16, smem image (128B swizzle, K-major)
     int64_t n_tiles = 0;
     uint64_t *crc_masks = nullptr;  // crc_len x W, codeword domain: syndrome bit b = parity(c & mask_b)
     DevStats *stats = nullptr;

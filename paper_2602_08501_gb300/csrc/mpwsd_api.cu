@@ -277,11 +277,11 @@ extern "C" int mpwsd_load_code(int n, const uint8_t *G, const uint8_t *frozen, i
             supp[(size_t)p * d.wq_max + q] = (uint32_t)idx[4 * q] | ((uint32_t)idx[4 * q + 1] << 8) |
                                              ((uint32_t)idx[4 * q + 2] << 16) | ((uint32_t)idx[4 * q + 3] << 24);
     }
-    // bf16 0/1 pattern tiles, kTcPatternsPerTile patterns x n per tile, laid
+    // bf16 0/1 pattern tiles, tc_patterns_per_tile(n) patterns x n per tile, laid
     // out as the shared memory image a K-major 128-byte-swizzled UMMA operand
     // expects: for each 64-element K chunk, rows of 128 B grouped in 1024-B
     // atoms, 16-B unit u of row r stored at unit u ^ (r % 8).
-    constexpr int TP = kTcPatternsPerTile;
+    const int TP = tc_patterns_per_tile(n);
     d.n_tiles = (n_patterns + TP - 1) / TP;
     const int kchunks = n / 64 > 0 ? n / 64 : 1;
     const size_t tile_elems = (size_t)TP * kchunks * 64;

@@ -10,25 +10,33 @@
 // finishes the row itself (FP64 re-rank, hop, compaction), so neither the
 // score matrix nor the candidates reach HBM.
 //
-// Kernel shape (sm_103a): persistent, one CTA per SM, 384 threads, units of
-// 256 rows (two 128-row blocks that share every pattern tile, halving the L2
-// traffic of the pattern stream per flop):
-//   warp 0      bulk-copy producer: 128-pattern tiles of P, stored in HBM as
-//               the exact shared-memory image of a K-major 128B-swizzled
-//               UMMA operand, streamed through a ring of smem stages;
+// Kernel shape (sm_103a): persistent, one CTA per SM, units of 256 rows (two
+// 128-row blocks that share every pattern tile, halving the L2 traffic of the
+// pattern stream per flop):
+//   warp 0      bulk-copy producer: pattern tiles of P (256 patterns for
+//               n = 64, 128 for n = 128), stored in HBM as the exact
+//               shared-memory image of a K-major 128B-swizzled UMMA operand,
+//               streamed through a two-stage smem ring;
 //   warp 1      TMEM allocator and single-thread MMA issuer
-//               (tcgen05.mma.cta_group::1.kind::f16, M = 128, N = 128, K = 16,
-//               two MMAs per K step, one per row block);
-//   warps 2-3   A builders (one per row block): gather frame and centre of
-//               4 rows per lane, then y rows 16 at a time, form z, split to
-//               bf16 hi / lo, write the swizzled A tiles;
-//   warps 4-11  epilogue (row block (warp-4)/4, TMEM lane quadrant warp%4):
-//               tcgen05.ld x64 of 32 TMEM lanes (one row per thread), minima
-//               of 8-column groups with three-input mins, and only groups
-//               that beat the row's 4th best enter the running top-K.
-// Two TMEM accumulators (2 x 256 columns) let the epilogue of tile j overlap
-// the MMAs of tile j+1. Every mbarrier wait is bounded in time; on expiry the
-// kernel records an error word, drains its own copies, frees TMEM and exits.
+//               (tcgen05.mma.cta_group::1.kind::f16, M = 128, K = 16);
+//   A builders  warps 2-3 (and 12-13 for n = 64): gather frame and centre of
+//               their rows, then y rows 16 at a time, form z, split to bf16
+//               hi / lo, write the swizzled A tiles;
+//   warps 4-11  epilogue: warp 4 + 4h + q reads TMEM lane quadrant q (one row
+//               per thread) and column half h of every accumulator with
+//               tcgen05.ld x64, takes minima of 8-column groups with
+//               three-input mins, and only groups that beat the row's
+//               admission threshold enter its running top-K; at the end of a
+//               unit the two halves of each row's list meet in shared memory.
+// MMAs into one accumulator serialise (one chain of 128 x 128 x 16 MMAs runs
+// at about 60 % of the tensor rate, 128 x 256 x 16 at the full rate), so the
+// issue order is chosen per n. n = 64: per tile, row block 0 then row block 1,
+// each one chain of 128 x 256 x 16 MMAs into its own 256-column accumulator;
+// the epilogue of one row block overlaps the other's MMAs. n = 128: per K
+// step one 128 x 128 x 16 MMA per row block (two chains), and two tile-sized
+// accumulators (2 x 256 columns) let the epilogue of tile j overlap the MMAs
+// of tile j+1. Every mbarrier wait is bounded in time; on expiry the kernel
+// records an error word, drains its own copies, frees TMEM and exits.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -42,21 +50,35 @@ static_assert(kTopK == 4, "the split merge loads one float4 / int4 per chunk lis
 constexpr int BM = 128;                 // rows per MMA (TMEM lanes)
 constexpr int RB = 2;                   // row blocks per unit, sharing every pattern tile
 constexpr int UM = BM * RB;             // rows per unit
-constexpr int BN = kTcPatternsPerTile;  // patterns per tile (MMA N)
-constexpr int kThreads = 384;                // 12 warps: producer, MMA, 2 builders, 8 epilogue
-constexpr int kEpiThreads = 256;
+constexpr int kEpiWarps = 8;                 // warps 4-11
+constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr unsigned long long kErrTcTimeout = 0x7C01;
 
 template <int N>
 struct TcCfg {
     static constexpr int KC = N / 64;                    // 64-element (128 B) K chunks
+    static constexpr int BN = tc_patterns_per_tile(N);   // patterns per tile (MMA N)
+    // SEQ: the row blocks take turns on the tensor core, one unbroken chain of
+    // MMAs per (tile, row block) into that row block's own accumulator, so the
+    // epilogue of one row block overlaps the other's MMAs (RB x BN = all 512
+    // TMEM columns). Otherwise the row blocks' MMAs interleave per K step and
+    // two tile-sized accumulators alternate.
+    static constexpr bool SEQ = (RB * BN == 512);
+    static_assert(SEQ || 2 * RB * BN <= 512, "accumulators exceed TMEM");
     static constexpr int A_BUFS = (N == 64) ? 2 : 1;
-    static constexpr int B_STAGES = (N == 64) ? 4 : 3;
+    static constexpr int B_STAGES = 2;
+    // A builders: one or two per row block (warps 2-3, then 12-13), each
+    // filling BM / (BUILDERS / RB) rows of its row block per unit
+    static constexpr int BUILDERS = (N == 64) ? 4 : 2;
+    static constexpr int QN = BM / 32 / (BUILDERS / RB);   // 32-row slices per builder
+    static constexpr int THREADS = (4 + kEpiWarps + BUILDERS - 2) * 32;
     static constexpr int A_PART_BYTES = BM * N * 2;      // one row block, hi or lo
     static constexpr int A_BUF_BYTES = RB * 2 * A_PART_BYTES;
     static constexpr int B_STAGE_BYTES = BN * N * 2;
     static constexpr int TILE_BYTES = A_BUFS * A_BUF_BYTES + B_STAGES * B_STAGE_BYTES;
-    static constexpr int SMEM_BYTES = TILE_BYTES + 1024 + 256;
+    static constexpr int BAR_BYTES = 256;
+    static constexpr int XCHG_BYTES = RB * BM * kTopK * 8;  // exchanged (value, index) lists
+    static constexpr int SMEM_BYTES = TILE_BYTES + 1024 + BAR_BYTES + XCHG_BYTES;
     static constexpr int G = (N == 64) ? 16 : 8;         // rows whose y loads are in flight together
 };
 
@@ -208,6 +230,38 @@ __device__ __forceinline__ void scan_groups(uint32_t (&v)[64], const float (&gm)
     }
 }
 
+// Admission of one 64-column chunk whose minimum m beats the row's threshold.
+// Once m is in the list nothing at or above t1 = min(thr, m + 2 eps) can
+// enter, so the chunk matters only through its columns below t1. Column e
+// lies in row group e / 8 (minima gm) and in strided set e % 8 (minima sm);
+// if exactly one row group and one strided set reach below t1, exactly one
+// column does: m itself, at 8 g + b, and it is inserted without a search.
+// Otherwise (a near-tie inside the chunk, or eps = 0) the groups are drained
+// one by one. Every lane runs the same instructions on the fast path, so a
+// warp pays for one admission per chunk however many of its rows have one.
+__device__ __forceinline__ void admit_chunk(uint32_t (&v)[64], const float (&gm)[8], float m, float (&tv)[kTopK],
+                                            int (&ti)[kTopK], float &thr, float eps2, int cbase) {
+    const float t1 = fminf(thr, __fadd_ru(m, eps2));
+    int na = 0, nb = 0, ga = 0, gb = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const float sm = fmin3(fmin3(__uint_as_float(v[b]), __uint_as_float(v[b + 8]), __uint_as_float(v[b + 16])),
+                               fmin3(__uint_as_float(v[b + 24]), __uint_as_float(v[b + 32]), __uint_as_float(v[b + 40])),
+                               fminf(__uint_as_float(v[b + 48]), __uint_as_float(v[b + 56])));
+        const bool pa = gm[b] < t1, pb = sm < t1;
+        na += pa;
+        ga += pa ? b : 0;
+        nb += pb;
+        gb += pb ? b : 0;
+    }
+    if (na == 1 && nb == 1) {
+        topk_insert<kTopK>(tv, ti, m, cbase + 8 * ga + gb);
+        thr = admit_thr(tv, eps2);
+    } else {
+        scan_groups<0>(v, gm, tv, ti, thr, eps2, cbase);
+    }
+}
+
 template <int G8>
 __device__ __forceinline__ void group_mins(const uint32_t (&v)[64], float (&gm)[8]) {
     if constexpr (G8 < 8) {
@@ -232,6 +286,9 @@ struct TcShared {
     int *abort_flag;
     int *last_flag;
     uint64_t *epi_pub, *epi_last;  // split: chunk lists published / last-chunk flag ready
+    uint64_t *xchg;                // epilogue halves: lists written / read (two phases per unit)
+    float *xv;                     // exchanged lists, RB x BM x kTopK
+    int *xi;
 };
 
 __device__ __forceinline__ void record_abort(const TcShared &sh, const CodeDev &c) {
@@ -240,7 +297,7 @@ __device__ __forceinline__ void record_abort(const TcShared &sh, const CodeDev &
 }
 
 template <int N>
-__global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a, const CodeDev c) {
+__global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const ScoreArgs a, const CodeDev c) {
     using C = TcCfg<N>;
     constexpr int W = (N + 63) / 64;
     constexpr int EPL = N / 32;  // elements of a row per lane in the A builder
@@ -258,15 +315,18 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
     sh.acc_empty = sh.acc_full + 2;
     sh.epi_pub = sh.acc_empty + 2;
     sh.epi_last = sh.epi_pub + 1;
-    sh.tmem_slot = (uint32_t *)(sh.epi_last + 1);
+    sh.xchg = sh.epi_last + 1;
+    sh.tmem_slot = (uint32_t *)(sh.xchg + 1);
     sh.abort_flag = (int *)(sh.tmem_slot + 1);
     sh.last_flag = sh.abort_flag + 1;
+    sh.xv = (float *)((uint8_t *)bars + C::BAR_BYTES);
+    sh.xi = (int *)(sh.xv + RB * BM * kTopK);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nrows = a.n_rows_dev ? *a.n_rows_dev : (int)a.n_rows;
     const int nunits = (nrows + UM - 1) / UM;
     const int P = (int)c.P;
-    const int nt = (P + BN - 1) / BN;
+    const int nt = (P + C::BN - 1) / C::BN;
     // Work items: (unit, chunk of pattern tiles). When there are fewer units than
     // the split target, each unit's tiles are split into nch chunks scanned by
     // different CTAs; the last CTA to finish a unit merges the chunks' lists.
@@ -283,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
             mbar_init(smem_u32(&sh.b_empty[s]), 1);
         }
         for (int s = 0; s < C::A_BUFS; ++s) {
-            mbar_init(smem_u32(&sh.a_full[s]), 64);
+            mbar_init(smem_u32(&sh.a_full[s]), 32 * C::BUILDERS);
             mbar_init(smem_u32(&sh.a_empty[s]), 1);
         }
         for (int s = 0; s < 2; ++s) {
@@ -292,6 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
         }
         mbar_init(smem_u32(sh.epi_pub), kEpiThreads);
         mbar_init(smem_u32(sh.epi_last), 1);
+        mbar_init(smem_u32(sh.xchg), kEpiThreads);
         *sh.abort_flag = 0;
         fence_mbar_init();
     }
@@ -339,9 +400,9 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
             }
         }
     } else if (warp == 1) {
-        // ---- MMA issuer: per tile and K step, one 128 x BN x 16 MMA per row block ----
+        // ---- MMA issuer (issue order per n: see the file comment) ----
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            constexpr uint32_t idesc = idesc_bf16(BM, C::BN);
             int gb = 0, gacc = 0;
             bool ok = true;
             uint32_t last_bar = 0, last_par = 0;
@@ -361,35 +422,66 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                         ok = false;
                         break;
                     }
-                    const int acc = gacc & 1;
-                    if (!mbar_wait(smem_u32(&sh.acc_empty[acc]), ((uint32_t)(gacc >> 1) & 1u) ^ 1u, abort_flag,
-                                   c.wait_limit_ns)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
                     const uint32_t bsm = smem_u32(Bbase + s * C::B_STAGE_BYTES);
+                    if constexpr (C::SEQ) {
+                        for (int rb = 0; rb < RB; ++rb) {
+                            if (!mbar_wait(smem_u32(&sh.acc_empty[rb]), ((uint32_t)gacc & 1u) ^ 1u, abort_flag,
+                                           c.wait_limit_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
 #pragma unroll
-                    for (int split = 0; split < 2; ++split) {
+                            for (int split = 0; split < 2; ++split) {
+                                const uint32_t apart = abuf + (uint32_t)((rb * 2 + split) * C::A_PART_BYTES);
 #pragma unroll
-                        for (int kc = 0; kc < C::KC; ++kc) {
+                                for (int kc = 0; kc < C::KC; ++kc) {
 #pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                const uint64_t bd = sw128_desc(bsm + kc * (BN * 128) + kk * 32);
-                                const uint32_t accum = (split | kc | kk) ? 1u : 0u;
+                                    for (int kk = 0; kk < 4; ++kk) {
+                                        const uint64_t bd = sw128_desc(bsm + kc * (C::BN * 128) + kk * 32);
+                                        const uint64_t ad = sw128_desc(apart + kc * (BM * 128) + kk * 32);
+                                        mma_bf16(tmem + (uint32_t)(rb * C::BN), ad, bd, idesc,
+                                                 (split | kc | kk) ? 1u : 0u);
+                                    }
+                                }
+                            }
+                            mma_commit(smem_u32(&sh.acc_full[rb]));
+                            last_bar = smem_u32(&sh.acc_full[rb]);
+                            last_par = (uint32_t)gacc & 1u;
+                        }
+                        if (!ok) break;
+                        mma_commit(smem_u32(&sh.b_empty[s]));
+                    } else {
+                        const int acc = gacc & 1;
+                        if (!mbar_wait(smem_u32(&sh.acc_empty[acc]), ((uint32_t)(gacc >> 1) & 1u) ^ 1u, abort_flag,
+                                       c.wait_limit_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
 #pragma unroll
-                                for (int rb = 0; rb < RB; ++rb) {
-                                    const uint32_t apart = abuf + (uint32_t)((rb * 2 + split) * C::A_PART_BYTES);
-                                    const uint64_t ad = sw128_desc(apart + kc * (BM * 128) + kk * 32);
-                                    mma_bf16(tmem + (uint32_t)(acc * RB * BN + rb * BN), ad, bd, idesc, accum);
+                        for (int split = 0; split < 2; ++split) {
+#pragma unroll
+                            for (int kc = 0; kc < C::KC; ++kc) {
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk) {
+                                    const uint64_t bd = sw128_desc(bsm + kc * (C::BN * 128) + kk * 32);
+                                    const uint32_t accum = (split | kc | kk) ? 1u : 0u;
+#pragma unroll
+                                    for (int rb = 0; rb < RB; ++rb) {
+                                        const uint32_t apart = abuf + (uint32_t)((rb * 2 + split) * C::A_PART_BYTES);
+                                        const uint64_t ad = sw128_desc(apart + kc * (BM * 128) + kk * 32);
+                                        mma_bf16(tmem + (uint32_t)(acc * RB * C::BN + rb * C::BN), ad, bd, idesc,
+                                                 accum);
+                                    }
                                 }
                             }
                         }
+                        mma_commit(smem_u32(&sh.b_empty[s]));
+                        mma_commit(smem_u32(&sh.acc_full[acc]));
+                        last_bar = smem_u32(&sh.acc_full[acc]);
+                        last_par = (uint32_t)(gacc >> 1) & 1u;
                     }
-                    mma_commit(smem_u32(&sh.b_empty[s]));
-                    mma_commit(smem_u32(&sh.acc_full[acc]));
-                    last_bar = smem_u32(&sh.acc_full[acc]);
-                    last_par = (uint32_t)(gacc >> 1) & 1u;
                 }
                 if (!ok) break;
                 mma_commit(smem_u32(&sh.a_empty[ab]));
@@ -403,9 +495,11 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                 }
             }
         }
-    } else if (warp < 4) {
-        // ---- A builders: warp 2 builds row block 0, warp 3 row block 1 of each unit ----
-        const int rb = warp - 2;
+    } else if (warp < 4 || warp >= 4 + kEpiWarps) {
+        // ---- A builders: builder b (warps 2, 3, 12, 13) fills row block b % RB,
+        // 32-row slices (b / RB) * QN .. + QN - 1 of it, for each unit ----
+        const int b = warp < 4 ? warp - 2 : warp - 4 - kEpiWarps + 2;
+        const int rb = b % RB, s0 = (b / RB) * C::QN;
         for (int i = 0; i < my_units; ++i) {
             const int ab = i % C::A_BUFS;
             bool ok = mbar_wait(smem_u32(&sh.a_empty[ab]), ((uint32_t)(i / C::A_BUFS) & 1u) ^ 1u, abort_flag,
@@ -417,12 +511,12 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
             }
             const int unit = ((int)blockIdx.x + i * (int)gridDim.x) / nch;
             const int row0 = unit * UM + rb * BM;
-            // each lane gathers the frame and centre of 4 rows at once
-            int fr[4];
-            uint64_t cwl[4][W];
+            // each lane gathers the frame and centre of QN rows at once
+            int fr[C::QN];
+            uint64_t cwl[C::QN][W];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int row = row0 + q * 32 + lane;
+            for (int q = 0; q < C::QN; ++q) {
+                const int row = row0 + (s0 + q) * 32 + lane;
                 fr[q] = -1;
 #pragma unroll
                 for (int w = 0; w < W; ++w) cwl[q][w] = 0;
@@ -440,11 +534,16 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
             const int kcl = j0 / 64, e64 = j0 % 64;
             const int unit16 = e64 / 8, within = (e64 % 8) * 2;
 #pragma unroll 1
-            for (int q = 0; q < 4; ++q) {
-                // rows q*32 .. q*32+31: their frame and centre sit in lane (r % 32), slot q
-                const int frq = q == 0 ? fr[0] : q == 1 ? fr[1] : q == 2 ? fr[2] : fr[3];
-                uint64_t cq0 = q == 0 ? cwl[0][0] : q == 1 ? cwl[1][0] : q == 2 ? cwl[2][0] : cwl[3][0];
-                uint64_t cq1 = q == 0 ? cwl[0][W - 1] : q == 1 ? cwl[1][W - 1] : q == 2 ? cwl[2][W - 1] : cwl[3][W - 1];
+            for (int q = 0; q < C::QN; ++q) {
+                // rows (s0+q)*32 .. +31: their frame and centre sit in lane (r % 32), slot q
+                int frq = fr[0];
+                uint64_t cq0 = cwl[0][0], cq1 = cwl[0][W - 1];
+#pragma unroll
+                for (int u = 1; u < C::QN; ++u) {
+                    frq = q == u ? fr[u] : frq;
+                    cq0 = q == u ? cwl[u][0] : cq0;
+                    cq1 = q == u ? cwl[u][W - 1] : cq1;
+                }
 #pragma unroll 1
                 for (int g0 = 0; g0 < 32; g0 += C::G) {
                     float v[C::G][EPL];
@@ -471,7 +570,7 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                     }
 #pragma unroll
                     for (int u = 0; u < C::G; ++u) {
-                        const int r = q * 32 + g0 + u;
+                        const int r = (s0 + q) * 32 + g0 + u;
                         // both words come from the row's owner lane; this lane keeps its chunk's word
                         uint64_t bits = __shfl_sync(0xffffffffu, cq0, g0 + u);
                         if constexpr (W > 1) {
@@ -503,77 +602,178 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
             mbar_arrive(smem_u32(&sh.a_full[ab]));
         }
     } else {
-        // ---- epilogue: TMEM -> registers -> running top-K, one row per thread ----
-        const int q = warp & 3;              // TMEM lane quadrant
-        const int rb = (warp - 4) >> 2;      // row block of this warp
-        const int r = q * 32 + lane;         // row within the row block
+        // ---- epilogue: TMEM -> registers -> running top-K lists ----
+        // Warp 4 + 4h + q reads TMEM lane quadrant q, column half h of every
+        // accumulator, so all eight warps work on each accumulator. A thread
+        // keeps partial lists for row q*32+lane of both row blocks; at the end
+        // of a unit it hands the one of row block 1-h to its partner (warp
+        // 4 + 4(1-h) + q, same lane) through shared memory and finishes row
+        // block h.
+        const int q = warp & 3;
+        const int h = (warp - 4) >> 2;
+        const int r = q * 32 + lane;
+        constexpr int HALF = C::BN / 2;  // columns per warp per accumulator
         int gacc = 0;
         bool ok = true;
         unsigned long long my_cand = 0, my_hops = 0;
         int nsplit = 0;  // split items finished by this CTA (phase of epi_pub / epi_last)
+        // decode: the rows' trajectories (loaded at the start of the unit
+        // before) and ||y||_1 of their frames from the workspace (loaded at the
+        // end of the unit before), so neither latency sits between two units
+        auto row_of = [&](int ii, int rbx) {
+            return (((int)blockIdx.x + ii * (int)gridDim.x) / nch) * UM + rbx * BM + r;
+        };
+        int t_next[RB];
+        float l1_next[RB];
+#pragma unroll
+        for (int rbx = 0; rbx < RB; ++rbx) {
+            t_next[rbx] = 0;
+            l1_next[rbx] = 0.0f;
+            if (a.fused && row_of(0, rbx) < nrows) {
+                t_next[rbx] = a.rows[row_of(0, rbx)];
+                l1_next[rbx] = a.ws.slot_l1[t_next[rbx] / a.L];
+            }
+        }
         for (int i = 0; i < my_units && ok; ++i) {
             const int item = (int)blockIdx.x + i * (int)gridDim.x;
             const int unit = item / nch, ch = item % nch;
-            const int row = unit * UM + rb * BM + r;
-            float tv[kTopK];
-            int ti[kTopK];
+            const int t_cur = h ? t_next[1] : t_next[0];
+            float tv[RB][kTopK], thr[RB], eps2[RB];
+            int ti[RB][kTopK];
 #pragma unroll
-            for (int k = 0; k < kTopK; ++k) {
-                tv[k] = CUDART_INF_F;
-                ti[k] = -1;
-            }
-            // 2 eps of this row (the re-rank margin), from ||y||_1 of its frame
-            float eps2 = 0.0f;
-            if (row < nrows) {
-                const int t = a.rows ? a.rows[row] : row;
-                const int f = a.row_frame ? a.row_frame[row] : a.slot_frame[t / a.L];
-                const float4 *y4 = reinterpret_cast<const float4 *>(a.y + (int64_t)f * N);
-                float l1 = 0.0f;
-#pragma unroll 4
-                for (int k4 = 0; k4 < N / 4; ++k4) {
-                    const float4 q4 = y4[k4];
-                    l1 += fabsf(grid_f(q4.x)) + fabsf(grid_f(q4.y)) + fabsf(grid_f(q4.z)) + fabsf(grid_f(q4.w));
+            for (int rbx = 0; rbx < RB; ++rbx) {
+#pragma unroll
+                for (int k = 0; k < kTopK; ++k) {
+                    tv[rbx][k] = CUDART_INF_F;
+                    ti[rbx][k] = -1;
                 }
-                eps2 = __fmul_ru(2.0f * kEpsScale, __fmul_ru(l1, 1.0f + 1.0f / 1024.0f));
+                thr[rbx] = CUDART_INF_F;
+                // 2 eps of this row (the re-rank margin), from ||y||_1 of its frame
+                eps2[rbx] = 0.0f;
+                const int row = row_of(i, rbx);
+                if (a.fused) {
+                    if (row < nrows) eps2[rbx] = __fmul_ru(2.0f * kEpsScale, __fmul_ru(l1_next[rbx], 1.0f + 1.0f / 1024.0f));
+                    if (i + 1 < my_units && row_of(i + 1, rbx) < nrows) t_next[rbx] = a.rows[row_of(i + 1, rbx)];
+                } else if (row < nrows) {
+                    const int t = a.rows ? a.rows[row] : row;
+                    const int f = a.row_frame ? a.row_frame[row] : a.slot_frame[t / a.L];
+                    const float4 *y4 = reinterpret_cast<const float4 *>(a.y + (int64_t)f * N);
+                    float l1 = 0.0f;
+#pragma unroll 4
+                    for (int k4 = 0; k4 < N / 4; ++k4) {
+                        const float4 q4 = y4[k4];
+                        l1 += fabsf(grid_f(q4.x)) + fabsf(grid_f(q4.y)) + fabsf(grid_f(q4.z)) + fabsf(grid_f(q4.w));
+                    }
+                    eps2[rbx] = __fmul_ru(2.0f * kEpsScale, __fmul_ru(l1, 1.0f + 1.0f / 1024.0f));
+                }
             }
-            float thr = CUDART_INF_F;
-            for (int j = ch * nt / nch; j < (ch + 1) * nt / nch; ++j, ++gacc) {
-                const int acc = gacc & 1;
-                bool w = mbar_wait(smem_u32(&sh.acc_full[acc]), (uint32_t)(gacc >> 1) & 1u, abort_flag, c.wait_limit_ns);
-                w = __all_sync(0xffffffffu, w);
-                if (!w) {
+            for (int j = ch * nt / nch; j < (ch + 1) * nt / nch && ok; ++j, ++gacc) {
+                const bool full = (j + 1) * C::BN <= P;
+                if constexpr (!C::SEQ) {
+                    bool w = mbar_wait(smem_u32(&sh.acc_full[gacc & 1]), (uint32_t)(gacc >> 1) & 1u, abort_flag,
+                                       c.wait_limit_ns);
+                    if (!__all_sync(0xffffffffu, w)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                }
+#pragma unroll
+                for (int rbx = 0; rbx < RB; ++rbx) {
+                    if constexpr (C::SEQ) {
+                        bool w = mbar_wait(smem_u32(&sh.acc_full[rbx]), (uint32_t)gacc & 1u, abort_flag, c.wait_limit_ns);
+                        if (!__all_sync(0xffffffffu, w)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    const uint32_t col = (C::SEQ ? (uint32_t)(rbx * C::BN) : (uint32_t)((gacc & 1) * RB * C::BN + rbx * C::BN)) +
+                                         (uint32_t)(h * HALF);
+#pragma unroll 1
+                    for (int cc = 0; cc < HALF / 64; ++cc) {
+                        uint32_t v[64];
+                        __syncwarp();
+                        tmem_ld64(tmem + ((uint32_t)(q * 32) << 16) + col + (uint32_t)(cc * 64), v);
+                        const int cbase = j * C::BN + h * HALF + cc * 64;
+                        if (!full) {
+#pragma unroll
+                            for (int e = 0; e < 64; ++e)
+                                if (cbase + e >= P) v[e] = __float_as_uint(CUDART_INF_F);
+                        }
+                        float gm[8];
+                        group_mins<0>(v, gm);
+                        const float m =
+                            fmin3(fmin3(gm[0], gm[1], gm[2]), fmin3(gm[3], gm[4], gm[5]), fminf(gm[6], gm[7]));
+                        if (m < thr[rbx]) admit_chunk(v, gm, m, tv[rbx], ti[rbx], thr[rbx], eps2[rbx], cbase);
+                    }
+                    if constexpr (C::SEQ) {
+                        tc_fence_before();
+                        mbar_arrive(smem_u32(&sh.acc_empty[rbx]));
+                    }
+                }
+                if constexpr (!C::SEQ) {
+                    if (ok) {
+                        tc_fence_before();
+                        mbar_arrive(smem_u32(&sh.acc_empty[gacc & 1]));
+                    }
+                }
+            }
+            if (!ok) break;
+            // exchange halves: publish the list of row block 1-h (after the partner
+            // has read the previous unit's), then merge the partner's of row block h
+            if (i > 0) {
+                bool w = mbar_wait(smem_u32(sh.xchg), 1u, abort_flag, c.wait_limit_ns);
+                if (!__all_sync(0xffffffffu, w)) {
                     ok = false;
                     break;
                 }
-                tc_fence_after();
-                const bool full = (j + 1) * BN <= P;
-#pragma unroll 1
-                for (int ch = 0; ch < BN / 64; ++ch) {
-                    uint32_t v[64];
-                    __syncwarp();
-                    tmem_ld64(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * RB * BN + rb * BN + ch * 64), v);
-                    const int cbase = j * BN + ch * 64;
-                    if (!full) {
-#pragma unroll
-                        for (int e = 0; e < 64; ++e)
-                            if (cbase + e >= P) v[e] = __float_as_uint(CUDART_INF_F);
-                    }
-                    float gm[8];
-                    group_mins<0>(v, gm);
-                    const float m = fmin3(fmin3(gm[0], gm[1], gm[2]), fmin3(gm[3], gm[4], gm[5]), fminf(gm[6], gm[7]));
-                    if (m < thr) scan_groups<0>(v, gm, tv, ti, thr, eps2, cbase);
-                }
-                tc_fence_before();
-                mbar_arrive(smem_u32(&sh.acc_empty[acc]));
             }
-            if (!ok) break;
+#pragma unroll
+            for (int k = 0; k < kTopK; ++k) {
+                sh.xv[((1 - h) * BM + r) * kTopK + k] = h ? tv[0][k] : tv[1][k];
+                sh.xi[((1 - h) * BM + r) * kTopK + k] = h ? ti[0][k] : ti[1][k];
+            }
+            mbar_arrive(smem_u32(sh.xchg));
+            {
+                bool w = mbar_wait(smem_u32(sh.xchg), 0u, abort_flag, c.wait_limit_ns);
+                if (!__all_sync(0xffffffffu, w)) {
+                    ok = false;
+                    break;
+                }
+            }
+            const int row = row_of(i, h);
+            float fv[kTopK];
+            int fi[kTopK];
+            const float feps2 = h ? eps2[1] : eps2[0];
+            float fthr = h ? thr[1] : thr[0];
+#pragma unroll
+            for (int k = 0; k < kTopK; ++k) {
+                fv[k] = h ? tv[1][k] : tv[0][k];
+                fi[k] = h ? ti[1][k] : ti[0][k];
+            }
+#pragma unroll
+            for (int k = 0; k < kTopK; ++k) {
+                const float pv = sh.xv[(h * BM + r) * kTopK + k];
+                const int pi = sh.xi[(h * BM + r) * kTopK + k];
+                if (pi >= 0 && pv < fthr) {
+                    topk_insert<kTopK>(fv, fi, pv, pi);
+                    fthr = admit_thr(fv, feps2);
+                }
+            }
+            mbar_arrive(smem_u32(sh.xchg));
+            if (a.fused) {
+#pragma unroll
+                for (int rbx = 0; rbx < RB; ++rbx)
+                    if (i + 1 < my_units && row_of(i + 1, rbx) < nrows) l1_next[rbx] = a.ws.slot_l1[t_next[rbx] / a.L];
+            }
             if (nch > 1) {
                 // publish this chunk's list; the last chunk of the unit merges them all
-                const size_t slot = ((size_t)item * UM + rb * BM + r) * kTopK;
+                const size_t slot = ((size_t)item * UM + h * BM + r) * kTopK;
 #pragma unroll
                 for (int k = 0; k < kTopK; ++k) {
-                    a.split_val[slot + k] = tv[k];
-                    a.split_idx[slot + k] = ti[k];
+                    a.split_val[slot + k] = fv[k];
+                    a.split_idx[slot + k] = fi[k];
                 }
                 __threadfence();
                 // all epilogue threads published -> one thread counts the chunk -> all read
@@ -599,17 +799,17 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                 __threadfence();
 #pragma unroll
                 for (int k = 0; k < kTopK; ++k) {
-                    tv[k] = CUDART_INF_F;
-                    ti[k] = -1;
+                    fv[k] = CUDART_INF_F;
+                    fi[k] = -1;
                 }
-                thr = CUDART_INF_F;
+                fthr = CUDART_INF_F;
                 // chunks in pattern order (ties keep the lower index), four chunks' loads in flight
                 for (int c0 = 0; c0 < nch; c0 += 4) {
                     float pv[4][kTopK];
                     int pi[4][kTopK];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const size_t src = ((size_t)(unit * nch + min(c0 + u, nch - 1)) * UM + rb * BM + r) * kTopK;
+                        const size_t src = ((size_t)(unit * nch + min(c0 + u, nch - 1)) * UM + h * BM + r) * kTopK;
                         const float4 v4 = __ldcg(reinterpret_cast<const float4 *>(a.split_val + src));
                         const int4 i4 = __ldcg(reinterpret_cast<const int4 *>(a.split_idx + src));
                         pv[u][0] = v4.x; pv[u][1] = v4.y; pv[u][2] = v4.z; pv[u][3] = v4.w;
@@ -620,9 +820,9 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                         if (c0 + u >= nch) break;
 #pragma unroll
                         for (int k = 0; k < kTopK; ++k) {
-                            if (pi[u][k] >= 0 && pv[u][k] < thr) {
-                                topk_insert<kTopK>(tv, ti, pv[u][k], pi[u][k]);
-                                thr = admit_thr(tv, eps2);
+                            if (pi[u][k] >= 0 && pv[u][k] < fthr) {
+                                topk_insert<kTopK>(fv, fi, pv[u][k], pi[u][k]);
+                                fthr = admit_thr(fv, feps2);
                             }
                         }
                     }
@@ -633,16 +833,19 @@ __global__ void __launch_bounds__(kThreads, 1) score_tc_kernel(const ScoreArgs a
                 // finish the row: FP64 re-rank of the kept candidates and the hop (Algorithm 1)
                 int outcome = kRowNone, t = 0;
                 if (row < nrows) {
-                    t = a.rows[row];
-                    outcome = resolve_row(a.ws, c, t, a.L, a.y, tv, ti, my_cand);
+                    t = t_cur;
+                    outcome = resolve_row(a.ws, c, t, a.L, a.y, fv, fi, my_cand);
                     my_hops += outcome == kRowHop;
                 }
                 route_row(a.ws, a.iter, outcome, t);
             } else if (row < nrows) {
+                // entries admitted before the minimum was seen may lie outside its band
+                const float band = __fadd_ru(fv[0], feps2);
 #pragma unroll
                 for (int k = 0; k < kTopK; ++k) {
-                    a.topk_val[(int64_t)row * kTopK + k] = tv[k];
-                    a.topk_idx[(int64_t)row * kTopK + k] = ti[k];
+                    const bool keep = k == 0 || fv[k] < band;
+                    a.topk_val[(int64_t)row * kTopK + k] = keep ? fv[k] : CUDART_INF_F;
+                    a.topk_idx[(int64_t)row * kTopK + k] = keep ? fi[k] : -1;
                 }
             }
         }
@@ -673,7 +876,7 @@ cudaError_t launch_n(const CodeDev &c, const ScoreArgs &a, cudaStream_t s) {
     int64_t grid = c.num_sms;
     if (!a.n_rows_dev) grid = std::min<int64_t>(grid, (a.n_rows + UM - 1) / UM);
     if (grid <= 0) return cudaSuccess;
-    score_tc_kernel<N><<<(unsigned)grid, kThreads, smem, s>>>(a, c);
+    score_tc_kernel<N><<<(unsigned)grid, TcCfg<N>::THREADS, smem, s>>>(a, c);
     return cudaGetLastError();
 }
 

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kHopThreads) rescan_kernel(const Workspace ws,
         double best = CUDART_INF;
         int bp = -1;
         for (int p = threadIdx.x; p < (int)c.P; p += blockDim.x) {
-            const double s = exact_score(yr, cw, c.pat_bits + (int64_t)p * c.W, c.W);
+            const double s = exact_score(yr, cw, c.W, c.pat_supp + (int64_t)p * c.wq_max, c.wq_max, c.n);
             if (s < best) {
                 best = s;
                 bp = p;
