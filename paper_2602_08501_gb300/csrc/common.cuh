@@ -41,29 +41,39 @@ __device__ __forceinline__ void topk_insert(float (&v)[K], int (&ix)[K], float s
 // added, so the sum is accumulated exactly in int32 and converted once; this is
 // the same number an FP64 summation gives (exact on the grid) at a fraction of
 // the FP64-pipe work. The support list of p (4 uint8 indices per word, padded
-// with index n) is decoded 16 indices at a time, so their 16 loads of y are in
-// flight together instead of one after another.
-__device__ __forceinline__ double exact_score(const float *yr, const uint64_t *c, int W, const uint32_t *supp,
-                                              int wq, int n) {
-    const uint64_t c0 = c[0], c1 = W > 1 ? c[1] : 0ull;
+// with index n) is taken 16 indices (4 words) at a time, so their 16 loads of
+// y are in flight together instead of one after another.
+__device__ __forceinline__ int exact_round(const float *yr, uint64_t c0, uint64_t c1, const uint32_t (&wd)[4], int n) {
+    float v[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int j = (int)((wd[e >> 2] >> (8 * (e & 3))) & 255u);
+        v[e] = j < n ? yr[j] : 0.0f;
+    }
+    int s = 0;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int j = (int)((wd[e >> 2] >> (8 * (e & 3))) & 255u);
+        const uint64_t word = (j & 64) ? c1 : c0;
+        const int g = grid_q(v[e]);  // 0 for padding
+        s += ((word >> (j & 63)) & 1ull) ? -g : g;
+    }
+    return s;
+}
+
+// Support words q0 .. q0+3 of a pattern (index 255 past its wq words: no sample).
+__device__ __forceinline__ void support_words(const uint32_t *supp, int wq, int q0, uint32_t (&wd)[4]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) wd[u] = q0 + u < wq ? supp[q0 + u] : 0xffffffffu;
+}
+
+__device__ __forceinline__ double exact_score(const float *yr, uint64_t c0, uint64_t c1, const uint32_t *supp, int wq,
+                                              int n) {
     int s = 0;
     for (int q0 = 0; q0 < wq; q0 += 4) {
         uint32_t wd[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) wd[u] = q0 + u < wq ? supp[q0 + u] : 0xffffffffu;
-        float v[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int j = (int)((wd[e >> 2] >> (8 * (e & 3))) & 255u);
-            v[e] = j < n ? yr[j] : 0.0f;
-        }
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int j = (int)((wd[e >> 2] >> (8 * (e & 3))) & 255u);
-            const uint64_t word = (j & 64) ? c1 : c0;
-            const int g = grid_q(v[e]);  // 0 for padding
-            s += ((word >> (j & 63)) & 1ull) ? -g : g;
-        }
+        support_words(supp, wq, q0, wd);
+        s += exact_round(yr, c0, c1, wd, n);
     }
     return (double)s * (1.0 / 524288.0);
 }
@@ -97,37 +107,6 @@ __device__ __forceinline__ bool apply_decision(const Workspace &ws, const CodeDe
 }
 
 enum RowOutcome { kRowNone = 0, kRowHop = 1, kRowStop = 2, kRowRescan = 3 };
-
-// Near-tie re-rank of one trajectory after its scoring step: the kernel kept
-// candidates (v, ix) ascending, every pattern whose approximate score is within
-// 2 eps of the smallest (eps = 2^-14 ||y||_1 of the frame). Each of them is
-// re-scored exactly in FP64; the smallest exact score (lowest index on ties)
-// decides the hop. If all kTopK slots lie within the band, more candidates may
-// exist and the row goes to the full FP64 rescan.
-__device__ __forceinline__ int resolve_row(const Workspace &ws, const CodeDev &c, int t, int L, const float *y,
-                                           const float (&v)[kTopK], const int (&ix)[kTopK],
-                                           unsigned long long &cand) {
-    const int slot = t / L;
-    const float *yr = y + (int64_t)ws.slot_frame[slot] * c.n;
-    const float eps = kEpsScale * ws.slot_l1[slot];
-    const float thr = __fadd_ru(v[0], __fmul_ru(2.0f, eps));
-    if (ix[kTopK - 1] >= 0 && v[kTopK - 1] <= thr) return kRowRescan;
-    double best = CUDART_INF;
-    int bp = -1;
-    const uint64_t *cw = ws.traj_cw + (int64_t)t * c.W;
-#pragma unroll
-    for (int q = 0; q < kTopK; ++q) {
-        if (ix[q] >= 0 && v[q] <= thr) {
-            const double s = exact_score(yr, cw, c.W, c.pat_supp + (int64_t)ix[q] * c.wq_max, c.wq_max, c.n);
-            ++cand;
-            if (s < best || (s == best && ix[q] < bp)) {
-                best = s;
-                bp = ix[q];
-            }
-        }
-    }
-    return apply_decision(ws, c, t, bp, best) ? kRowHop : kRowStop;
-}
 
 // Append trajectory t to the next active list (hop) or the rescan list, with
 // warp-aggregated atomics; every lane of the warp calls this together.

@@ -117,14 +117,9 @@ struct ScoreArgs {
     const int *slot_frame;    // frame of trajectory id t = slot_frame[t / L] (decode) ...
     const int32_t *row_frame; // ... or frame of row r = row_frame[r] (direct)
     int L;
-    float *topk_val;          // row-indexed (direct mode)
+    float *topk_val;          // row-indexed: the kept (value, index) list of each row
     int *topk_idx;
     unsigned long long *evals; // stats counter (may be null)
-    // decode mode: the scoring kernel finishes each row with the FP64 re-rank
-    // and the hop of Algorithm 1 (fused = 1) instead of writing its top-K
-    int fused;
-    int iter;
-    Workspace ws;
     // split buffers (both modes; nullptr: every CTA scans whole units)
     float *split_val;
     int *split_idx;

@@ -526,15 +526,14 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
         a.L = L;
         a.topk_val = ws.topk_val;
         a.topk_idx = ws.topk_idx;
-        a.fused = 1;  // the scoring kernel re-ranks, hops and compacts each row itself
-        a.iter = it;
-        a.ws = ws;
         a.split_val = ws.split_val;
         a.split_idx = ws.split_idx;
         a.unit_done = ws.unit_done;
         a.split_items = d.split_items;
         e = launch_score(code, o.score_mode, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "scoring launch");
+        e = timed_launch(code, MPWSD_KERNEL_HOP, s, [&] { return launch_hop(d, ws, it, L, y_dev, s); });
+        if (e != cudaSuccess) return cuda_fail(e, "hop launch");
         e = timed_launch(code, MPWSD_KERNEL_RESCAN, s, [&] { return launch_rescan(d, ws, it, L, y_dev, s); });
         if (e != cudaSuccess) return cuda_fail(e, "rescan launch");
     }

@@ -6,8 +6,8 @@
 // i.e. -G(p)/2 with G the correlation gain of Eq. (5); ED(c xor p) - ED(c)
 // = 4 S(p) (translation identity, Eq. (3)). The kernel keeps, per row, the K
 // smallest scores that lie within 2 eps of the row's smallest (eps the re-rank
-// margin) with their pattern indices, never writes S itself, and in a decode
-// finishes each row with the FP64 re-rank and the hop.
+// margin) with their pattern indices and never writes S itself; the re-rank
+// and the hop of a decode follow in their own kernel.
 //
 // Mapping: one thread per row, 128 rows per CTA. The CTA stages its rows'
 // z vectors in shared memory (row stride n+1 floats: conflict-free per-thread
@@ -38,7 +38,6 @@ __global__ void __launch_bounds__(kRows) score_fp32_kernel(const ScoreArgs a, co
     const int nblk = (nrows + kRows - 1) / kRows;
     const int tid = threadIdx.x;
     float *zr = zs + tid * ZS;
-    unsigned long long my_cand = 0, my_hops = 0;
     for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
         const int r = rb * kRows + tid;
         const bool live = r < nrows;
@@ -97,29 +96,15 @@ __global__ void __launch_bounds__(kRows) score_fp32_kernel(const ScoreArgs a, co
                 }
             }
         }
-        if (a.fused) {
-            // finish the row: FP64 re-rank of the kept candidates and the hop (Algorithm 1)
-            int outcome = kRowNone, t = 0;
-            if (live) {
-                t = a.rows[r];
-                outcome = resolve_row(a.ws, c, t, a.L, a.y, tv, ti, my_cand);
-                my_hops += outcome == kRowHop;
-            }
-            route_row(a.ws, a.iter, outcome, t);
-        } else if (live) {
+        if (live) {
+            // entries admitted before the minimum was seen may lie outside its band
+            const float band = __fadd_ru(tv[0], eps2);
 #pragma unroll
             for (int q = 0; q < kTopK; ++q) {
-                a.topk_val[(int64_t)r * kTopK + q] = tv[q];
-                a.topk_idx[(int64_t)r * kTopK + q] = ti[q];
+                const bool keep = q == 0 || tv[q] < band;
+                a.topk_val[(int64_t)r * kTopK + q] = keep ? tv[q] : CUDART_INF_F;
+                a.topk_idx[(int64_t)r * kTopK + q] = keep ? ti[q] : -1;
             }
-        }
-    }
-    if (a.fused) {
-        const unsigned long long wc = __reduce_add_sync(0xffffffffu, (unsigned)my_cand);
-        const unsigned long long wh = __reduce_add_sync(0xffffffffu, (unsigned)my_hops);
-        if ((threadIdx.x & 31) == 0) {
-            if (wc) atomicAdd(&c.stats->rerank_candidates, wc);
-            if (wh) atomicAdd(&c.stats->hops, wh);
         }
     }
 }

@@ -6,9 +6,10 @@
 // S = Z P^T, a dense contraction. z is split as z = hi + lo with hi, lo
 // bf16 (|z - hi - lo| <= 2^-16 |z|), so S ~= [Z_hi | Z_lo] [P | P]^T is two
 // bf16 MMAs per K step into one FP32 accumulator; P is exact in bf16. The
-// epilogue keeps each row's candidates for the exact argmin and, in a decode,
-// finishes the row itself (FP64 re-rank, hop, compaction), so neither the
-// score matrix nor the candidates reach HBM.
+// epilogue keeps each row's candidates for the exact argmin (at most four, the
+// ones within the re-rank margin of the row's minimum), so the score matrix
+// never reaches HBM; the FP64 re-rank and the hop follow in their own kernel,
+// where a grid of short rows hides their memory latency.
 //
 // Kernel shape (sm_103a): persistent, one CTA per SM, units of 256 rows (two
 // 128-row blocks that share every pattern tile, halving the L2 traffic of the
@@ -77,9 +78,12 @@ struct TcCfg {
     static constexpr int B_STAGE_BYTES = BN * N * 2;
     static constexpr int TILE_BYTES = A_BUFS * A_BUF_BYTES + B_STAGES * B_STAGE_BYTES;
     static constexpr int BAR_BYTES = 256;
+    static_assert((2 * B_STAGES + 3 * A_BUFS + 7) * 8 + 12 <= BAR_BYTES, "mbarriers and flags fit their region");
     static constexpr int XCHG_BYTES = RB * BM * kTopK * 8;  // exchanged (value, index) lists
-    static constexpr int SMEM_BYTES = TILE_BYTES + 1024 + BAR_BYTES + XCHG_BYTES;
-    static constexpr int G = (N == 64) ? 16 : 8;         // rows whose y loads are in flight together
+    static constexpr int L1_BYTES = A_BUFS * UM * 4;  // ||y||_1 of each row of the A buffers
+    static constexpr int BEST_BYTES = RB * BM * 2 * 8;  // shared running minima of the row halves
+    static constexpr int SMEM_BYTES = TILE_BYTES + 1024 + BAR_BYTES + XCHG_BYTES + L1_BYTES + BEST_BYTES;
+    static constexpr int G = 8;                          // rows whose y loads are in flight together
 };
 
 // ---- PTX wrappers -------------------------------------------------------------
@@ -287,8 +291,11 @@ struct TcShared {
     int *last_flag;
     uint64_t *epi_pub, *epi_last;  // split: chunk lists published / last-chunk flag ready
     uint64_t *xchg;                // epilogue halves: lists written / read (two phases per unit)
+    uint64_t *l1_free;             // per A buffer: every epilogue thread has read its rows' norms
     float *xv;                     // exchanged lists, RB x BM x kTopK
     int *xi;
+    float *l1;                     // ||y||_1 of the rows of each A buffer, A_BUFS x UM
+    unsigned long long *best;      // (work item, best value so far) of each row half, RB x BM x 2
 };
 
 __device__ __forceinline__ void record_abort(const TcShared &sh, const CodeDev &c) {
@@ -316,11 +323,14 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
     sh.epi_pub = sh.acc_empty + 2;
     sh.epi_last = sh.epi_pub + 1;
     sh.xchg = sh.epi_last + 1;
-    sh.tmem_slot = (uint32_t *)(sh.xchg + 1);
+    sh.l1_free = sh.xchg + 1;
+    sh.tmem_slot = (uint32_t *)(sh.l1_free + C::A_BUFS);
     sh.abort_flag = (int *)(sh.tmem_slot + 1);
     sh.last_flag = sh.abort_flag + 1;
     sh.xv = (float *)((uint8_t *)bars + C::BAR_BYTES);
     sh.xi = (int *)(sh.xv + RB * BM * kTopK);
+    sh.l1 = (float *)(sh.xi + RB * BM * kTopK);
+    sh.best = (unsigned long long *)(sh.l1 + C::A_BUFS * UM);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nrows = a.n_rows_dev ? *a.n_rows_dev : (int)a.n_rows;
@@ -337,6 +347,7 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
         nitems > (int)blockIdx.x ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     if (my_units == 0) return;
 
+    for (int e = threadIdx.x; e < RB * BM * 2; e += blockDim.x) sh.best[e] = ~0ull;  // no work item
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::B_STAGES; ++s) {
             mbar_init(smem_u32(&sh.b_full[s]), 1);
@@ -345,6 +356,7 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
         for (int s = 0; s < C::A_BUFS; ++s) {
             mbar_init(smem_u32(&sh.a_full[s]), 32 * C::BUILDERS);
             mbar_init(smem_u32(&sh.a_empty[s]), 1);
+            mbar_init(smem_u32(&sh.l1_free[s]), kEpiThreads);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(smem_u32(&sh.acc_full[s]), 1);
@@ -500,20 +512,12 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
         // 32-row slices (b / RB) * QN .. + QN - 1 of it, for each unit ----
         const int b = warp < 4 ? warp - 2 : warp - 4 - kEpiWarps + 2;
         const int rb = b % RB, s0 = (b / RB) * C::QN;
-        for (int i = 0; i < my_units; ++i) {
-            const int ab = i % C::A_BUFS;
-            bool ok = mbar_wait(smem_u32(&sh.a_empty[ab]), ((uint32_t)(i / C::A_BUFS) & 1u) ^ 1u, abort_flag,
-                                c.wait_limit_ns);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) {
-                if (lane == 0) record_abort(sh, c);
-                break;
-            }
-            const int unit = ((int)blockIdx.x + i * (int)gridDim.x) / nch;
-            const int row0 = unit * UM + rb * BM;
-            // each lane gathers the frame and centre of QN rows at once
-            int fr[C::QN];
-            uint64_t cwl[C::QN][W];
+        // frame and centre of this lane's QN rows of a unit; gathered for the
+        // next unit as soon as one is built, so the loads overlap the wait
+        int fr[C::QN];
+        uint64_t cwl[C::QN][W];
+        auto gather = [&](int ii) {
+            const int row0 = (((int)blockIdx.x + ii * (int)gridDim.x) / nch) * UM + rb * BM;
 #pragma unroll
             for (int q = 0; q < C::QN; ++q) {
                 const int row = row0 + (s0 + q) * 32 + lane;
@@ -528,76 +532,109 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
                     for (int w = 0; w < W; ++w) cwl[q][w] = cw[w];
                 }
             }
+        };
+        const int j0 = lane * EPL;  // this lane's elements of every row
+        const int kcl = j0 / 64, e64 = j0 % 64;
+        const int unit16 = e64 / 8, within = (e64 % 8) * 2;
+        constexpr int GPS = 32 / C::G;          // groups of G rows per 32-row slice
+        constexpr int NGRP = C::QN * GPS;       // groups per unit
+        // y values of group gi (rows (s0 + gi / GPS) * 32 + (gi % GPS) * G + u):
+        // their frames sit in lanes (gi % GPS) * G + u of slot gi / GPS
+        auto load_group = [&](int gi, float (&dst)[C::G][EPL]) {
+            const int qq = gi / GPS, g0 = (gi % GPS) * C::G;
+            int frq = fr[0];
+#pragma unroll
+            for (int u = 1; u < C::QN; ++u) frq = qq == u ? fr[u] : frq;
+#pragma unroll
+            for (int u = 0; u < C::G; ++u) {
+                const int f = __shfl_sync(0xffffffffu, frq, g0 + u);
+                if (f >= 0) {
+                    const float *yr = a.y + (int64_t)f * N + j0;
+                    if constexpr (EPL == 2) {
+                        const float2 t2 = *reinterpret_cast<const float2 *>(yr);
+                        dst[u][0] = t2.x;
+                        dst[u][1] = t2.y;
+                    } else {
+                        const float4 t4 = *reinterpret_cast<const float4 *>(yr);
+                        dst[u][0] = t4.x;
+                        dst[u][1] = t4.y;
+                        dst[u][2] = t4.z;
+                        dst[u][3] = t4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) dst[u][e] = 0.0f;
+                }
+            }
+        };
+        if (my_units > 0) gather(0);
+        for (int i = 0; i < my_units; ++i) {
+            const int ab = i % C::A_BUFS;
+            // the buffer is free once its MMAs are done and the epilogue has read its norms
+            bool ok = mbar_wait(smem_u32(&sh.a_empty[ab]), ((uint32_t)(i / C::A_BUFS) & 1u) ^ 1u, abort_flag,
+                                c.wait_limit_ns) &&
+                      mbar_wait(smem_u32(&sh.l1_free[ab]), ((uint32_t)(i / C::A_BUFS) & 1u) ^ 1u, abort_flag,
+                                c.wait_limit_ns);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) record_abort(sh, c);
+                break;
+            }
             uint8_t *Ahi = Abase + ab * C::A_BUF_BYTES + (rb * 2 + 0) * C::A_PART_BYTES;
             uint8_t *Alo = Abase + ab * C::A_BUF_BYTES + (rb * 2 + 1) * C::A_PART_BYTES;
-            const int j0 = lane * EPL;  // this lane's elements of every row
-            const int kcl = j0 / 64, e64 = j0 % 64;
-            const int unit16 = e64 / 8, within = (e64 % 8) * 2;
+            // groups of G rows, the y loads of group gi+1 in flight while group gi is converted
+            float cur[C::G][EPL], nxt[C::G][EPL];
+            load_group(0, cur);
 #pragma unroll 1
-            for (int q = 0; q < C::QN; ++q) {
-                // rows (s0+q)*32 .. +31: their frame and centre sit in lane (r % 32), slot q
-                int frq = fr[0];
+            for (int gi = 0; gi < NGRP; ++gi) {
+                if (gi + 1 < NGRP) load_group(gi + 1, nxt);
+                const int qq = gi / GPS, g0 = (gi % GPS) * C::G;
                 uint64_t cq0 = cwl[0][0], cq1 = cwl[0][W - 1];
 #pragma unroll
                 for (int u = 1; u < C::QN; ++u) {
-                    frq = q == u ? fr[u] : frq;
-                    cq0 = q == u ? cwl[u][0] : cq0;
-                    cq1 = q == u ? cwl[u][W - 1] : cq1;
+                    cq0 = qq == u ? cwl[u][0] : cq0;
+                    cq1 = qq == u ? cwl[u][W - 1] : cq1;
                 }
-#pragma unroll 1
-                for (int g0 = 0; g0 < 32; g0 += C::G) {
-                    float v[C::G][EPL];
 #pragma unroll
-                    for (int u = 0; u < C::G; ++u) {
-                        const int f = __shfl_sync(0xffffffffu, frq, g0 + u);
-                        if (f >= 0) {
-                            const float *yr = a.y + (int64_t)f * N + j0;
-                            if constexpr (EPL == 2) {
-                                const float2 t2 = *reinterpret_cast<const float2 *>(yr);
-                                v[u][0] = t2.x;
-                                v[u][1] = t2.y;
-                            } else {
-                                const float4 t4 = *reinterpret_cast<const float4 *>(yr);
-                                v[u][0] = t4.x;
-                                v[u][1] = t4.y;
-                                v[u][2] = t4.z;
-                                v[u][3] = t4.w;
-                            }
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < EPL; ++e) v[u][e] = 0.0f;
-                        }
+                for (int u = 0; u < C::G; ++u) {
+                    const int r = (s0 + qq) * 32 + g0 + u;
+                    // both words come from the row's owner lane; this lane keeps its chunk's word
+                    uint64_t bits = __shfl_sync(0xffffffffu, cq0, g0 + u);
+                    if constexpr (W > 1) {
+                        const uint64_t hi_word = __shfl_sync(0xffffffffu, cq1, g0 + u);
+                        bits = kcl ? hi_word : bits;
                     }
+                    uint32_t hi[EPL], lo[EPL];
+                    int l1q = 0;  // this lane's part of sum_j |round(y_j 2^19)|
 #pragma unroll
-                    for (int u = 0; u < C::G; ++u) {
-                        const int r = (s0 + q) * 32 + g0 + u;
-                        // both words come from the row's owner lane; this lane keeps its chunk's word
-                        uint64_t bits = __shfl_sync(0xffffffffu, cq0, g0 + u);
-                        if constexpr (W > 1) {
-                            const uint64_t hi_word = __shfl_sync(0xffffffffu, cq1, g0 + u);
-                            bits = kcl ? hi_word : bits;
-                        }
-                        uint32_t hi[EPL], lo[EPL];
-#pragma unroll
-                        for (int e = 0; e < EPL; ++e) {
-                            const float y = grid_f(v[u][e]);
-                            const float z = ((bits >> ((j0 + e) & 63)) & 1ull) ? -y : y;
-                            split_bf16(z, hi[e], lo[e]);
-                        }
-                        // element j of row r: chunk j/64, 16-B unit (j%64)/8 stored at unit ^ (r%8)
-                        const int off =
-                            kcl * (BM * 128) + (r / 8) * 1024 + (r % 8) * 128 + ((unit16 ^ (r % 8)) * 16) + within;
-                        if constexpr (EPL == 2) {
-                            *(uint32_t *)(Ahi + off) = hi[0] | (hi[1] << 16);
-                            *(uint32_t *)(Alo + off) = lo[0] | (lo[1] << 16);
-                        } else {
-                            *(uint2 *)(Ahi + off) = make_uint2(hi[0] | (hi[1] << 16), hi[2] | (hi[3] << 16));
-                            *(uint2 *)(Alo + off) = make_uint2(lo[0] | (lo[1] << 16), lo[2] | (lo[3] << 16));
-                        }
+                    for (int e = 0; e < EPL; ++e) {
+                        const int g = grid_q(cur[u][e]);
+                        l1q += abs(g);
+                        const float y = (float)g * (1.0f / 524288.0f);
+                        const float z = ((bits >> ((j0 + e) & 63)) & 1ull) ? -y : y;
+                        split_bf16(z, hi[e], lo[e]);
+                    }
+                    // ||y||_1 of the row for the epilogue's re-rank margin (exact: |sum| < 2^30)
+                    l1q = __reduce_add_sync(0xffffffffu, l1q);
+                    if (lane == 0) sh.l1[ab * UM + rb * BM + r] = (float)l1q * (1.0f / 524288.0f);
+                    // element j of row r: chunk j/64, 16-B unit (j%64)/8 stored at unit ^ (r%8)
+                    const int off =
+                        kcl * (BM * 128) + (r / 8) * 1024 + (r % 8) * 128 + ((unit16 ^ (r % 8)) * 16) + within;
+                    if constexpr (EPL == 2) {
+                        *(uint32_t *)(Ahi + off) = hi[0] | (hi[1] << 16);
+                        *(uint32_t *)(Alo + off) = lo[0] | (lo[1] << 16);
+                    } else {
+                        *(uint2 *)(Ahi + off) = make_uint2(hi[0] | (hi[1] << 16), hi[2] | (hi[3] << 16));
+                        *(uint2 *)(Alo + off) = make_uint2(lo[0] | (lo[1] << 16), lo[2] | (lo[3] << 16));
                     }
                 }
                 (void)cq1;
+#pragma unroll
+                for (int u = 0; u < C::G; ++u)
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) cur[u][e] = nxt[u][e];
             }
+            if (i + 1 < my_units) gather(i + 1);
             fence_proxy_async();
             mbar_arrive(smem_u32(&sh.a_full[ab]));
         }
@@ -615,29 +652,22 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
         constexpr int HALF = C::BN / 2;  // columns per warp per accumulator
         int gacc = 0;
         bool ok = true;
-        unsigned long long my_cand = 0, my_hops = 0;
         int nsplit = 0;  // split items finished by this CTA (phase of epi_pub / epi_last)
-        // decode: the rows' trajectories (loaded at the start of the unit
-        // before) and ||y||_1 of their frames from the workspace (loaded at the
-        // end of the unit before), so neither latency sits between two units
         auto row_of = [&](int ii, int rbx) {
             return (((int)blockIdx.x + ii * (int)gridDim.x) / nch) * UM + rbx * BM + r;
         };
-        int t_next[RB];
-        float l1_next[RB];
-#pragma unroll
-        for (int rbx = 0; rbx < RB; ++rbx) {
-            t_next[rbx] = 0;
-            l1_next[rbx] = 0.0f;
-            if (a.fused && row_of(0, rbx) < nrows) {
-                t_next[rbx] = a.rows[row_of(0, rbx)];
-                l1_next[rbx] = a.ws.slot_l1[t_next[rbx] / a.L];
-            }
-        }
         for (int i = 0; i < my_units && ok; ++i) {
             const int item = (int)blockIdx.x + i * (int)gridDim.x;
             const int unit = item / nch, ch = item % nch;
-            const int t_cur = h ? t_next[1] : t_next[0];
+            // the builders leave ||y||_1 of this unit's rows beside its A tiles
+            const int ab = i % C::A_BUFS;
+            {
+                bool w = mbar_wait(smem_u32(&sh.a_full[ab]), (uint32_t)(i / C::A_BUFS) & 1u, abort_flag, c.wait_limit_ns);
+                if (!__all_sync(0xffffffffu, w)) {
+                    ok = false;
+                    break;
+                }
+            }
             float tv[RB][kTopK], thr[RB], eps2[RB];
             int ti[RB][kTopK];
 #pragma unroll
@@ -649,24 +679,9 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
                 }
                 thr[rbx] = CUDART_INF_F;
                 // 2 eps of this row (the re-rank margin), from ||y||_1 of its frame
-                eps2[rbx] = 0.0f;
-                const int row = row_of(i, rbx);
-                if (a.fused) {
-                    if (row < nrows) eps2[rbx] = __fmul_ru(2.0f * kEpsScale, __fmul_ru(l1_next[rbx], 1.0f + 1.0f / 1024.0f));
-                    if (i + 1 < my_units && row_of(i + 1, rbx) < nrows) t_next[rbx] = a.rows[row_of(i + 1, rbx)];
-                } else if (row < nrows) {
-                    const int t = a.rows ? a.rows[row] : row;
-                    const int f = a.row_frame ? a.row_frame[row] : a.slot_frame[t / a.L];
-                    const float4 *y4 = reinterpret_cast<const float4 *>(a.y + (int64_t)f * N);
-                    float l1 = 0.0f;
-#pragma unroll 4
-                    for (int k4 = 0; k4 < N / 4; ++k4) {
-                        const float4 q4 = y4[k4];
-                        l1 += fabsf(grid_f(q4.x)) + fabsf(grid_f(q4.y)) + fabsf(grid_f(q4.z)) + fabsf(grid_f(q4.w));
-                    }
-                    eps2[rbx] = __fmul_ru(2.0f * kEpsScale, __fmul_ru(l1, 1.0f + 1.0f / 1024.0f));
-                }
+                eps2[rbx] = __fmul_ru(2.0f * kEpsScale, __fmul_ru(sh.l1[ab * UM + rbx * BM + r], 1.0f + 1.0f / 1024.0f));
             }
+            mbar_arrive(smem_u32(&sh.l1_free[ab]));
             for (int j = ch * nt / nch; j < (ch + 1) * nt / nch && ok; ++j, ++gacc) {
                 const bool full = (j + 1) * C::BN <= P;
                 if constexpr (!C::SEQ) {
@@ -678,7 +693,10 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
                     }
                     tc_fence_after();
                 }
-#pragma unroll
+                // one copy of the chunk code: the current row block's list is always
+                // entry 0 (the two swap after each row block)
+                static_assert(RB == 2, "two row blocks swap places");
+#pragma unroll 1
                 for (int rbx = 0; rbx < RB; ++rbx) {
                     if constexpr (C::SEQ) {
                         bool w = mbar_wait(smem_u32(&sh.acc_full[rbx]), (uint32_t)gacc & 1u, abort_flag, c.wait_limit_ns);
@@ -690,6 +708,14 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
                     }
                     const uint32_t col = (C::SEQ ? (uint32_t)(rbx * C::BN) : (uint32_t)((gacc & 1) * RB * C::BN + rbx * C::BN)) +
                                          (uint32_t)(h * HALF);
+                    // the other half's best so far is an upper bound on the row's
+                    // minimum: nothing at or above it + 2 eps can be a candidate
+                    volatile unsigned long long *best = sh.best + (rbx * BM + r) * 2;
+                    {
+                        const unsigned long long pb = best[1 - h];
+                        if ((int)(pb >> 32) == item)
+                            thr[0] = fminf(thr[0], __fadd_ru(__uint_as_float((uint32_t)pb), eps2[0]));
+                    }
 #pragma unroll 1
                     for (int cc = 0; cc < HALF / 64; ++cc) {
                         uint32_t v[64];
@@ -705,12 +731,28 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
                         group_mins<0>(v, gm);
                         const float m =
                             fmin3(fmin3(gm[0], gm[1], gm[2]), fmin3(gm[3], gm[4], gm[5]), fminf(gm[6], gm[7]));
-                        if (m < thr[rbx]) admit_chunk(v, gm, m, tv[rbx], ti[rbx], thr[rbx], eps2[rbx], cbase);
+                        if (m < thr[0]) admit_chunk(v, gm, m, tv[0], ti[0], thr[0], eps2[0], cbase);
                     }
                     if constexpr (C::SEQ) {
                         tc_fence_before();
                         mbar_arrive(smem_u32(&sh.acc_empty[rbx]));
                     }
+                    best[h] = ((unsigned long long)(uint32_t)item << 32) | __float_as_uint(tv[0][0]);
+#pragma unroll
+                    for (int e = 0; e < kTopK; ++e) {
+                        const float sv = tv[0][e];
+                        tv[0][e] = tv[1][e];
+                        tv[1][e] = sv;
+                        const int si = ti[0][e];
+                        ti[0][e] = ti[1][e];
+                        ti[1][e] = si;
+                    }
+                    const float st = thr[0];
+                    thr[0] = thr[1];
+                    thr[1] = st;
+                    const float se = eps2[0];
+                    eps2[0] = eps2[1];
+                    eps2[1] = se;
                 }
                 if constexpr (!C::SEQ) {
                     if (ok) {
@@ -762,11 +804,6 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
                 }
             }
             mbar_arrive(smem_u32(sh.xchg));
-            if (a.fused) {
-#pragma unroll
-                for (int rbx = 0; rbx < RB; ++rbx)
-                    if (i + 1 < my_units && row_of(i + 1, rbx) < nrows) l1_next[rbx] = a.ws.slot_l1[t_next[rbx] / a.L];
-            }
             if (nch > 1) {
                 // publish this chunk's list; the last chunk of the unit merges them all
                 const size_t slot = ((size_t)item * UM + h * BM + r) * kTopK;
@@ -829,16 +866,7 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
                 }
                 if (threadIdx.x == 4 * 32) a.unit_done[unit] = 0;  // ready for the next launch
             }
-            if (a.fused) {
-                // finish the row: FP64 re-rank of the kept candidates and the hop (Algorithm 1)
-                int outcome = kRowNone, t = 0;
-                if (row < nrows) {
-                    t = t_cur;
-                    outcome = resolve_row(a.ws, c, t, a.L, a.y, fv, fi, my_cand);
-                    my_hops += outcome == kRowHop;
-                }
-                route_row(a.ws, a.iter, outcome, t);
-            } else if (row < nrows) {
+            if (row < nrows) {
                 // entries admitted before the minimum was seen may lie outside its band
                 const float band = __fadd_ru(fv[0], feps2);
 #pragma unroll
@@ -850,14 +878,6 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
             }
         }
         if (!ok && lane == 0) record_abort(sh, c);
-        if (a.fused) {
-            const unsigned long long wc = __reduce_add_sync(0xffffffffu, (unsigned)my_cand);
-            const unsigned long long wh = __reduce_add_sync(0xffffffffu, (unsigned)my_hops);
-            if (lane == 0) {
-                if (wc) atomicAdd(&c.stats->rerank_candidates, wc);
-                if (wh) atomicAdd(&c.stats->hops, wh);
-            }
-        }
     }
 
     tc_fence_before();

@@ -13,30 +13,87 @@ namespace {
 
 constexpr int kHopThreads = 256;
 
-// Re-rank and decision from a top-K written by a scoring kernel (used when the
-// scoring kernel did not finish the rows itself).
+// Re-rank and decision for each active row, from the list its scoring step
+// kept: the candidates are the leading entries within 2 eps of the first
+// (eps = 2^-14 ||y||_1 of the frame); each is scored exactly, the smallest
+// exact score (lowest index on ties) is taken, and the row hops if it is < 0
+// (a strict ED decrease), else stops. A full list within the band means more
+// candidates may exist: the row goes to the FP64 rescan instead.
+// One thread per row; its reads are issued in dependency waves so a thread
+// keeps several in flight: (1) trajectory id and list, (2) what they name --
+// frame and ||y||_1, centre, D, state word, the first candidate's support --
+// (3) the samples of that support.
 __global__ void __launch_bounds__(kHopThreads) hop_kernel(const Workspace ws, const CodeDev c, int iter, int L,
                                                           const float *y) {
     const int nrows = ws.counters[1 + iter];
     const int *act_in = ws.act[iter & 1];
     const int stride = gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
+    const int W = c.W, wq = c.wq_max, n = c.n;
     unsigned long long my_cand = 0, my_hops = 0;
     // iterate in whole warps so the aggregated appends see converged lanes
     for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nrows; base += stride) {
         const int r = base + lane;
         int outcome = kRowNone, t = 0;
         if (r < nrows) {
+            // wave 1
             t = act_in[r];
-            float v[kTopK];
-            int ix[kTopK];
+            const float4 v = reinterpret_cast<const float4 *>(ws.topk_val)[r];
+            const int4 ix = reinterpret_cast<const int4 *>(ws.topk_idx)[r];
+            // wave 2
+            const int slot = t / L;
+            const int frame = ws.slot_frame[slot];
+            const float l1 = ws.slot_l1[slot];
+            uint64_t *cwp = ws.traj_cw + (int64_t)t * W;
+            const uint64_t c0 = cwp[0], c1 = W > 1 ? cwp[1] : 0ull;
+            const double D = ws.traj_D[t];
+            const uint32_t st = ws.traj_state[t];
+            uint32_t wd0[4];
+            support_words(c.pat_supp + (int64_t)max(ix.x, 0) * wq, wq, 0, wd0);
+            const float *yr = y + (int64_t)frame * n;
+            const float thr = __fadd_ru(v.x, __fmul_ru(2.0f, kEpsScale * l1));
+            if (ix.w >= 0 && v.w <= thr) {
+                outcome = kRowRescan;
+            } else {
+                // the candidates are the leading entries (the list is ascending)
+                const int ncand = (ix.x >= 0 && v.x <= thr) + (ix.y >= 0 && v.y <= thr) + (ix.z >= 0 && v.z <= thr);
+                double best = CUDART_INF;
+                int bp = -1;
+#pragma unroll 1
+                for (int q = 0; q < ncand; ++q) {
+                    const int p = q == 0 ? ix.x : q == 1 ? ix.y : ix.z;
+                    const uint32_t *supp = c.pat_supp + (int64_t)p * wq;
+                    // wave 3 for the first candidate: its first support words are in hand
+                    int sum = 0;
+                    for (int q0 = 0; q0 < wq; q0 += 4) {
+                        uint32_t wd[4];
+                        if (q == 0 && q0 == 0) {
 #pragma unroll
-            for (int q = 0; q < kTopK; ++q) {
-                v[q] = ws.topk_val[(int64_t)r * kTopK + q];
-                ix[q] = ws.topk_idx[(int64_t)r * kTopK + q];
+                            for (int u = 0; u < 4; ++u) wd[u] = wd0[u];
+                        } else {
+                            support_words(supp, wq, q0, wd);
+                        }
+                        sum += exact_round(yr, c0, c1, wd, n);
+                    }
+                    const double s = (double)sum * (1.0 / 524288.0);
+                    if (s < best || (s == best && p < bp)) {
+                        best = s;
+                        bp = p;
+                    }
+                }
+                my_cand += (unsigned long long)ncand;
+                outcome = kRowStop;
+                if (bp >= 0 && best < 0.0) {
+                    // hop to c xor p (a strict ED decrease of 4 |S|)
+                    const uint64_t *pb = c.pat_bits + (int64_t)bp * W;
+                    cwp[0] = c0 ^ pb[0];
+                    if (W > 1) cwp[1] = c1 ^ pb[1];
+                    ws.traj_D[t] = D + 2.0 * best;
+                    ws.traj_state[t] = st + 1u;  // hops counter in the low byte (<= MPWSD_MAX_T)
+                    outcome = kRowHop;
+                    ++my_hops;
+                }
             }
-            outcome = resolve_row(ws, c, t, L, y, v, ix, my_cand);
-            my_hops += outcome == kRowHop;
         }
         route_row(ws, iter, outcome, t);
     }
@@ -65,7 +122,7 @@ __global__ void __launch_bounds__(kHopThreads) rescan_kernel(const Workspace ws,
         double best = CUDART_INF;
         int bp = -1;
         for (int p = threadIdx.x; p < (int)c.P; p += blockDim.x) {
-            const double s = exact_score(yr, cw, c.W, c.pat_supp + (int64_t)p * c.wq_max, c.wq_max, c.n);
+            const double s = exact_score(yr, cw[0], c.W > 1 ? cw[1] : 0ull, c.pat_supp + (int64_t)p * c.wq_max, c.wq_max, c.n);
             if (s < best) {
                 best = s;
                 bp = p;

@@ -202,7 +202,7 @@ def test_stats_counters(mp, rm26, rm26_or):
     assert st["stage2_frames"] == int(np.sum(fl & 1))
     assert st["trajectories"] == 8 * st["stage2_frames"]
     assert st["pattern_evals"] == int(ref["evals"].sum())
-    assert st["kernel_launches"] >= 1 + 2 * 4 + 1  # stage 1, T x (score + re-rank, rescan), final
+    assert st["kernel_launches"] >= 1 + 3 * 4 + 1  # stage 1, T x (score, re-rank + hop, rescan), final
 
 
 def test_graph_replay_matches_direct_launches(mp, rm26):
