@@ -359,8 +359,9 @@ def run_ours(args, wl_cfg):
     sm_clock_max = peaks["sm_max_mhz"] * 1e6
     alu_peak = 152 * 128 * sm_clock_max  # lane-ops/s: 152 SMs x 128 INT32/FP32 lanes x max SM clock
     evals = stats["pattern_evals"]
-    wbar = float(np.mean([bin(int(p[0])).count("1") + (bin(int(p[1])).count("1") if W > 1 else 0)
-                          for p in code.patterns])) if P else 0.0
+    wts = [bin(int(p[0])).count("1") + (bin(int(p[1])).count("1") if W > 1 else 0) for p in code.patterns]
+    wbar = float(np.mean(wts)) if P else 0.0
+    wmax = max(wts) if P else 0
 
     def roofline_for(kname):
         ms = kinds[kname]["ms"]
@@ -391,11 +392,28 @@ def run_ours(args, wl_cfg):
             return {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "Top/s",
                     "frac": ach / (alu_peak / 1e12), "traffic": tr, "kernel": "scl",
                     "peak_kind": "152 SMs x 128 INT32 lanes x max SM clock", "ops_per_launch": ops}
+        if kname == "hop":
+            # bytes a row needs: its list entry (4 + 32), centre, D, state, 1/L of its frame's y row and
+            # slot data, the supports of its candidates, and on a hop the written centre, D, state, entry
+            rows = evals / P if P else 0.0
+            wq = math.ceil(wmax / 4)
+            cand = stats["rerank_candidates"] / rows if rows else 0.0
+            hopf = stats["hops"] / rows if rows else 0.0
+            bpr = 36 + 8 * W + 12 + (4 * n + 8) / L + cand * 4 * wq + hopf * (8 * W + 16)
+            ach = bpr * rows / launches / per_launch_s / 1e9
+            src = src_hash("paper_2602_08501_gb300/csrc/traj.cu", "paper_2602_08501_gb300/csrc/common.cuh",
+                           "paper_2602_08501_gb300/csrc/internal.h")
+            rec = recorded_traffic("hop", src, "row")
+            tr = None if rec is None else rec * rows / launches
+            return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"],
+                    "traffic": tr, "kernel": "hop", "peak_kind": f"HBM copy, {peaks['source']}",
+                    "bytes_per_row": bpr}
         return {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
                 "kernel": kname}
 
     roof = roofline_for(dominant)
-    others = [roofline_for(k) for k in ("scl", "score_tc", "score_fp32") if k in kinds and k != dominant]
+    others = [roofline_for(k) for k in ("scl", "score_tc", "score_fp32", "hop") if k in kinds and k != dominant]
 
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
