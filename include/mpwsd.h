@@ -203,7 +203,7 @@ MPWSD_API int mpwsd_decode_ws(mpwsd_code *code, mpwsd_workspace *ws, const float
  * that every GPU loading the library keeps until the process exits; this
  * entry point never calls cudaMalloc, cudaFree or any allocating routine.
  *  - Capacity: B frames with list size L must fit in 4 MiB of scratch (about
- *    50,000 to 60,000 trajectories B*L); larger requests return MPWSD_EINVAL
+ *    43,000 (L = 8) to 58,000 (L = 32) trajectories B*L); larger requests return MPWSD_EINVAL
  *    with the sizes in mpwsd_last_error().
  *  - Set-up: the first call on each device (with that device current) looks
  *    up the array's device address; make that first call before any stream
@@ -244,7 +244,8 @@ MPWSD_API int mpwsd_stage1_list(mpwsd_code *code, const float *y_dev, int64_t B,
  *   cw_dev      device, M x W uint64.     M          rows, >= 0.
  *   topk_val_dev device, M x MPWSD_TOPK FP32; topk_idx_dev device, M x
  *   MPWSD_TOPK int32 (-1 in the unused tail slots).
- * Asynchronous.
+ * Asynchronous. BF16X2 takes B*(4n + 4) bytes of stream-ordered scratch
+ * (cudaMallocAsync / cudaFreeAsync on the stream) for y in split form.
  */
 MPWSD_API int mpwsd_score_topk(mpwsd_code *code, int score_mode, const float *y_dev, int64_t B, const int32_t *frame_dev,
                      const uint64_t *cw_dev, int64_t M, float *topk_val_dev, int32_t *topk_idx_dev, void *stream);

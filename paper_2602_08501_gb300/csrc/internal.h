@@ -49,6 +49,7 @@ struct Workspace {
     int *counters = nullptr;    // [0] = failing frames F, [1 + i] = active rows before iteration i (i <= T), [32 + i] = rescan rows in iteration i
     int *slot_frame = nullptr;  // F: frame index of each failing-frame slot
     float *slot_l1 = nullptr;   // F: ||y||_1 of the frame
+    uint32_t *slot_yhl = nullptr;  // F x n: y of the frame as bf16 hi / lo parts (n/2 words each, two per word)
     uint64_t *traj_cw = nullptr;  // F*L x W: trajectory centres
     double *traj_D = nullptr;     // F*L: -sum_j y_j x_j (ED = ||y||^2 + n + 2 D)
     uint32_t *traj_state = nullptr;  // F*L: hops | rescan | valid
@@ -96,6 +97,7 @@ struct SclArgs {
     const float *y;
     int64_t B;
     int L;
+    int write_yhl;       // decode: also store each failing frame's y as bf16 hi / lo (tensor-core scoring)
     int mode;            // 0 = decode (CRC + compaction), 1 = list output
     int rule;            // MPWSD_RULE_*
     int use_crc;         // stage-1 early exit enabled
@@ -117,6 +119,10 @@ struct ScoreArgs {
     const int *slot_frame;    // frame of trajectory id t = slot_frame[t / L] (decode) ...
     const int32_t *row_frame; // ... or frame of row r = row_frame[r] (direct)
     int L;
+    // tensor-core scoring: y of each slot (decode: trajectory t is in slot t / L;
+    // direct: row r reads slot row_frame[r]) as bf16 hi / lo words, and ||y||_1
+    const uint32_t *yhl;
+    const float *l1;
     float *topk_val;          // row-indexed: the kept (value, index) list of each row
     int *topk_idx;
     unsigned long long *evals; // stats counter (may be null)
@@ -131,6 +137,8 @@ struct ScoreArgs {
 cudaError_t launch_scl(const CodeDev &c, const SclArgs &a, cudaStream_t s);
 cudaError_t launch_score_fp32(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
 cudaError_t launch_score_tc(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
+// y (B x n) -> bf16 hi / lo words and ||y||_1 per frame, for direct-mode tensor-core scoring
+cudaError_t launch_split_prep(const CodeDev &c, const float *y, int64_t B, uint32_t *yhl, float *l1, cudaStream_t s);
 bool score_tc_supported(const CodeDev &c);
 int rm_specialisation(int n, uint64_t lo, uint64_t hi);
 cudaError_t launch_hop(const CodeDev &c, const Workspace &ws, int iter, int L, const float *y, cudaStream_t s);

@@ -378,6 +378,7 @@ static size_t ws_layout(const CodeDev &d, int64_t max_B, int max_L, Workspace *w
     const size_t o_cnt = take(64 * sizeof(int));
     const size_t o_sf = take((size_t)max_B * sizeof(int));
     const size_t o_l1 = take((size_t)max_B * sizeof(float));
+    const size_t o_yhl = take((size_t)max_B * d.n * 4);
     const size_t o_cw = take((size_t)M * d.W * 8);
     const size_t o_D = take((size_t)M * 8);
     const size_t o_st = take((size_t)M * 4);
@@ -391,6 +392,7 @@ static size_t ws_layout(const CodeDev &d, int64_t max_B, int max_L, Workspace *w
         w->counters = (int *)(b + o_cnt);
         w->slot_frame = (int *)(b + o_sf);
         w->slot_l1 = (float *)(b + o_l1);
+        w->slot_yhl = (uint32_t *)(b + o_yhl);
         w->traj_cw = (uint64_t *)(b + o_cw);
         w->traj_D = (double *)(b + o_D);
         w->traj_state = (uint32_t *)(b + o_st);
@@ -514,6 +516,7 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
     sa.cw_out = cw_dev;
     sa.flags_out = flags_dev;
     sa.ws = ws;
+    sa.write_yhl = o.score_mode == MPWSD_SCORE_BF16X2;
     e = timed_launch(code, MPWSD_KERNEL_SCL, s, [&] { return launch_scl(d, sa, s); });
     if (e != cudaSuccess) return cuda_fail(e, "stage-1 launch");
     for (int it = 0; it < T; ++it) {
@@ -526,6 +529,8 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
         a.L = L;
         a.topk_val = ws.topk_val;
         a.topk_idx = ws.topk_idx;
+        a.yhl = ws.slot_yhl;
+        a.l1 = ws.slot_l1;
         a.split_val = ws.split_val;
         a.split_idx = ws.split_idx;
         a.unit_done = ws.unit_done;
@@ -682,7 +687,7 @@ extern "C" int mpwsd_score_topk(mpwsd_code *code, int score_mode, const float *y
         return fail(MPWSD_EINVAL, "score_mode = %d", score_mode);
     if (score_mode == MPWSD_SCORE_BF16X2 && !score_tc_supported(code->d))
         return fail(MPWSD_EUNSUPPORTED, "BF16X2 tensor-core scoring needs n = 64 or 128");
-    if (M < 0 || B < 0 || M > 0x7fffffffLL) return fail(MPWSD_EINVAL, "bad sizes");
+    if (M < 0 || B < 0 || M > 0x7fffffffLL || (M > 0 && B == 0)) return fail(MPWSD_EINVAL, "bad sizes");
     if (M > 0 && (!y_dev || !frame_dev || !cw_dev || !topk_val_dev || !topk_idx_dev))
         return fail(MPWSD_EINVAL, "NULL buffer");
     if (M == 0) return MPWSD_OK;
@@ -696,7 +701,26 @@ extern "C" int mpwsd_score_topk(mpwsd_code *code, int score_mode, const float *y
     a.L = 1;
     a.topk_val = topk_val_dev;
     a.topk_idx = topk_idx_dev;
-    cudaError_t e = launch_score(code, score_mode, a, (cudaStream_t)stream);
+    const cudaStream_t s = (cudaStream_t)stream;
+    void *prep = nullptr;
+    if (score_mode == MPWSD_SCORE_BF16X2) {
+        // stream-ordered scratch for y in split form: B x n words, then B norms
+        const size_t yhl_bytes = align256((size_t)B * code->d.n * 4);
+        cudaError_t e = cudaMallocAsync(&prep, yhl_bytes + (size_t)B * 4, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+        a.yhl = (const uint32_t *)prep;
+        a.l1 = (const float *)((char *)prep + yhl_bytes);
+        e = launch_split_prep(code->d, y_dev, B, (uint32_t *)prep, (float *)((char *)prep + yhl_bytes), s);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(prep, s);
+            return cuda_fail(e, "split launch");
+        }
+    }
+    cudaError_t e = launch_score(code, score_mode, a, s);
+    if (prep) {
+        const cudaError_t ef = cudaFreeAsync(prep, s);
+        if (e == cudaSuccess) e = ef;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "scoring launch");
     return MPWSD_OK;
 }

@@ -16,6 +16,7 @@
 // subtree is pending, left-subtree codewords of ancestors whose right subtree
 // is running). Integer LLRs: inputs on the 2^-19 grid are exact int32, path
 // metrics int64, so the list equals the FP64 formulation bit for bit.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
@@ -347,6 +348,24 @@ __global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32) scl_kernel(const
         for (int j = 0; j < N; ++j) l1 += abs(cx.ych[j]);
         a.ws.slot_frame[slot] = (int)frame;
         a.ws.slot_l1[slot] = (float)l1 * (1.0f / 524288.0f);
+    }
+    if (a.write_yhl) {
+        // y in the split form the tensor-core scoring consumes: word w holds
+        // elements 2w (low half) and 2w+1 of hi = bf16(y) and of lo = bf16(y - hi)
+        uint32_t *dst = a.ws.slot_yhl + (int64_t)slot * N;
+        for (int w = sl; w < N / 2; w += LW) {
+            uint32_t h2 = 0, l2 = 0;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float v = (float)cx.ych[2 * w + e] * (1.0f / 524288.0f);
+                const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+                h2 |= (uint32_t)__bfloat16_as_ushort(h) << (16 * e);
+                l2 |= (uint32_t)__bfloat16_as_ushort(l) << (16 * e);
+            }
+            dst[w] = h2;
+            dst[N / 2 + w] = l2;
+        }
     }
     if (sl < a.L) {
         const int64_t t = (int64_t)slot * a.L + pos;

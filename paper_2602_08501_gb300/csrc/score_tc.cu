@@ -512,21 +512,24 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
         // 32-row slices (b / RB) * QN .. + QN - 1 of it, for each unit ----
         const int b = warp < 4 ? warp - 2 : warp - 4 - kEpiWarps + 2;
         const int rb = b % RB, s0 = (b / RB) * C::QN;
-        // frame and centre of this lane's QN rows of a unit; gathered for the
-        // next unit as soon as one is built, so the loads overlap the wait
-        int fr[C::QN];
+        // slot, ||y||_1 and centre of this lane's QN rows of a unit; gathered for
+        // the next unit as soon as one is built, so the loads overlap the wait
+        int sl[C::QN];
+        float l1r[C::QN];
         uint64_t cwl[C::QN][W];
         auto gather = [&](int ii) {
             const int row0 = (((int)blockIdx.x + ii * (int)gridDim.x) / nch) * UM + rb * BM;
 #pragma unroll
             for (int q = 0; q < C::QN; ++q) {
                 const int row = row0 + (s0 + q) * 32 + lane;
-                fr[q] = -1;
+                sl[q] = -1;
+                l1r[q] = 0.0f;
 #pragma unroll
                 for (int w = 0; w < W; ++w) cwl[q][w] = 0;
                 if (row < nrows) {
                     const int t = a.rows ? a.rows[row] : row;
-                    fr[q] = a.row_frame ? a.row_frame[row] : a.slot_frame[t / a.L];
+                    sl[q] = a.row_frame ? a.row_frame[row] : t / a.L;
+                    l1r[q] = a.l1[sl[q]];
                     const uint64_t *cw = a.cw + (int64_t)t * W;
 #pragma unroll
                     for (int w = 0; w < W; ++w) cwl[q][w] = cw[w];
@@ -536,34 +539,35 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
         const int j0 = lane * EPL;  // this lane's elements of every row
         const int kcl = j0 / 64, e64 = j0 % 64;
         const int unit16 = e64 / 8, within = (e64 % 8) * 2;
+        constexpr int WPL = EPL / 2;            // hi (and lo) words of a row per lane
         constexpr int GPS = 32 / C::G;          // groups of G rows per 32-row slice
         constexpr int NGRP = C::QN * GPS;       // groups per unit
-        // y values of group gi (rows (s0 + gi / GPS) * 32 + (gi % GPS) * G + u):
-        // their frames sit in lanes (gi % GPS) * G + u of slot gi / GPS
-        auto load_group = [&](int gi, float (&dst)[C::G][EPL]) {
+        // split y of group gi (rows (s0 + gi / GPS) * 32 + (gi % GPS) * G + u):
+        // their slots sit in lanes (gi % GPS) * G + u of slot gi / GPS
+        auto load_group = [&](int gi, uint32_t (&dh)[C::G][WPL], uint32_t (&dl)[C::G][WPL]) {
             const int qq = gi / GPS, g0 = (gi % GPS) * C::G;
-            int frq = fr[0];
+            int slq = sl[0];
 #pragma unroll
-            for (int u = 1; u < C::QN; ++u) frq = qq == u ? fr[u] : frq;
+            for (int u = 1; u < C::QN; ++u) slq = qq == u ? sl[u] : slq;
 #pragma unroll
             for (int u = 0; u < C::G; ++u) {
-                const int f = __shfl_sync(0xffffffffu, frq, g0 + u);
-                if (f >= 0) {
-                    const float *yr = a.y + (int64_t)f * N + j0;
-                    if constexpr (EPL == 2) {
-                        const float2 t2 = *reinterpret_cast<const float2 *>(yr);
-                        dst[u][0] = t2.x;
-                        dst[u][1] = t2.y;
+                const int slot = __shfl_sync(0xffffffffu, slq, g0 + u);
+                if (slot >= 0) {
+                    const uint32_t *src = a.yhl + (int64_t)slot * N;
+                    if constexpr (WPL == 1) {
+                        dh[u][0] = src[lane];
+                        dl[u][0] = src[N / 2 + lane];
                     } else {
-                        const float4 t4 = *reinterpret_cast<const float4 *>(yr);
-                        dst[u][0] = t4.x;
-                        dst[u][1] = t4.y;
-                        dst[u][2] = t4.z;
-                        dst[u][3] = t4.w;
+                        const uint2 h2 = reinterpret_cast<const uint2 *>(src)[lane];
+                        const uint2 l2 = reinterpret_cast<const uint2 *>(src + N / 2)[lane];
+                        dh[u][0] = h2.x;
+                        dh[u][1] = h2.y;
+                        dl[u][0] = l2.x;
+                        dl[u][1] = l2.y;
                     }
                 } else {
 #pragma unroll
-                    for (int e = 0; e < EPL; ++e) dst[u][e] = 0.0f;
+                    for (int w = 0; w < WPL; ++w) dh[u][w] = dl[u][w] = 0u;
                 }
             }
         };
@@ -580,14 +584,19 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
                 if (lane == 0) record_abort(sh, c);
                 break;
             }
+            // ||y||_1 of this lane's rows, for the epilogue's re-rank margin
+#pragma unroll
+            for (int q = 0; q < C::QN; ++q) sh.l1[ab * UM + rb * BM + (s0 + q) * 32 + lane] = l1r[q];
             uint8_t *Ahi = Abase + ab * C::A_BUF_BYTES + (rb * 2 + 0) * C::A_PART_BYTES;
             uint8_t *Alo = Abase + ab * C::A_BUF_BYTES + (rb * 2 + 1) * C::A_PART_BYTES;
-            // groups of G rows, the y loads of group gi+1 in flight while group gi is converted
-            float cur[C::G][EPL], nxt[C::G][EPL];
-            load_group(0, cur);
+            // z = y x(c) in split form is the split of y with the sign bits of the
+            // elements where c_j = 1 flipped (bf16 rounding is symmetric);
+            // groups of G rows, the loads of group gi+1 in flight while gi is stored
+            uint32_t ch[C::G][WPL], cl[C::G][WPL], nh[C::G][WPL], nl[C::G][WPL];
+            load_group(0, ch, cl);
 #pragma unroll 1
             for (int gi = 0; gi < NGRP; ++gi) {
-                if (gi + 1 < NGRP) load_group(gi + 1, nxt);
+                if (gi + 1 < NGRP) load_group(gi + 1, nh, nl);
                 const int qq = gi / GPS, g0 = (gi % GPS) * C::G;
                 uint64_t cq0 = cwl[0][0], cq1 = cwl[0][W - 1];
 #pragma unroll
@@ -604,35 +613,33 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
                         const uint64_t hi_word = __shfl_sync(0xffffffffu, cq1, g0 + u);
                         bits = kcl ? hi_word : bits;
                     }
-                    uint32_t hi[EPL], lo[EPL];
-                    int l1q = 0;  // this lane's part of sum_j |round(y_j 2^19)|
+                    const uint32_t cb = (uint32_t)(bits >> (j0 & 63));  // c of this lane's elements, bit e
+                    uint32_t hw[WPL], lw[WPL];
 #pragma unroll
-                    for (int e = 0; e < EPL; ++e) {
-                        const int g = grid_q(cur[u][e]);
-                        l1q += abs(g);
-                        const float y = (float)g * (1.0f / 524288.0f);
-                        const float z = ((bits >> ((j0 + e) & 63)) & 1ull) ? -y : y;
-                        split_bf16(z, hi[e], lo[e]);
+                    for (int w = 0; w < WPL; ++w) {
+                        const uint32_t flip = ((cb >> (2 * w)) & 1u) << 15 | ((cb >> (2 * w + 1)) & 1u) << 31;
+                        hw[w] = ch[u][w] ^ flip;
+                        lw[w] = cl[u][w] ^ flip;
                     }
-                    // ||y||_1 of the row for the epilogue's re-rank margin (exact: |sum| < 2^30)
-                    l1q = __reduce_add_sync(0xffffffffu, l1q);
-                    if (lane == 0) sh.l1[ab * UM + rb * BM + r] = (float)l1q * (1.0f / 524288.0f);
                     // element j of row r: chunk j/64, 16-B unit (j%64)/8 stored at unit ^ (r%8)
                     const int off =
                         kcl * (BM * 128) + (r / 8) * 1024 + (r % 8) * 128 + ((unit16 ^ (r % 8)) * 16) + within;
-                    if constexpr (EPL == 2) {
-                        *(uint32_t *)(Ahi + off) = hi[0] | (hi[1] << 16);
-                        *(uint32_t *)(Alo + off) = lo[0] | (lo[1] << 16);
+                    if constexpr (WPL == 1) {
+                        *(uint32_t *)(Ahi + off) = hw[0];
+                        *(uint32_t *)(Alo + off) = lw[0];
                     } else {
-                        *(uint2 *)(Ahi + off) = make_uint2(hi[0] | (hi[1] << 16), hi[2] | (hi[3] << 16));
-                        *(uint2 *)(Alo + off) = make_uint2(lo[0] | (lo[1] << 16), lo[2] | (lo[3] << 16));
+                        *(uint2 *)(Ahi + off) = make_uint2(hw[0], hw[1]);
+                        *(uint2 *)(Alo + off) = make_uint2(lw[0], lw[1]);
                     }
                 }
                 (void)cq1;
 #pragma unroll
                 for (int u = 0; u < C::G; ++u)
 #pragma unroll
-                    for (int e = 0; e < EPL; ++e) cur[u][e] = nxt[u][e];
+                    for (int w = 0; w < WPL; ++w) {
+                        ch[u][w] = nh[u][w];
+                        cl[u][w] = nl[u][w];
+                    }
             }
             if (i + 1 < my_units) gather(i + 1);
             fence_proxy_async();
@@ -900,7 +907,42 @@ cudaError_t launch_n(const CodeDev &c, const ScoreArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// y -> bf16 hi / lo words and the exact ||y||_1 of each frame (one warp per frame)
+__global__ void __launch_bounds__(256) split_prep_kernel(const float *y, int64_t B, int n, uint32_t *yhl, float *l1) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; f < B; f += warps) {
+        const float *yr = y + f * n;
+        uint32_t *dst = yhl + f * n;
+        int acc = 0;
+        for (int w = lane; w < n / 2; w += 32) {
+            uint32_t h2 = 0, l2 = 0;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int g = grid_q(yr[2 * w + e]);
+                acc += abs(g);
+                const float v = (float)g * (1.0f / 524288.0f);
+                uint32_t hb, lb;
+                split_bf16(v, hb, lb);
+                h2 |= hb << (16 * e);
+                l2 |= lb << (16 * e);
+            }
+            dst[w] = h2;
+            dst[n / 2 + w] = l2;
+        }
+        acc = __reduce_add_sync(0xffffffffu, acc);  // exact: |sum| < 2^30
+        if (lane == 0) l1[f] = (float)acc * (1.0f / 524288.0f);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_split_prep(const CodeDev &c, const float *y, int64_t B, uint32_t *yhl, float *l1, cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((B + 7) / 8, (int64_t)c.num_sms * 16);
+    split_prep_kernel<<<(unsigned)blocks, 256, 0, s>>>(y, B, c.n, yhl, l1);
+    return cudaGetLastError();
+}
 
 bool score_tc_supported(const CodeDev &c) { return (c.n == 64 || c.n == 128) && c.pat_tiles != nullptr; }
 
