@@ -80,6 +80,14 @@ template <int N>
 struct PathState {
     int llr[N];                    // node of size S < N keeps its LLRs at [S, 2S)
     uint64_t beta[Log2<N>::v];     // beta[log2 H]: codeword of the finished left child of size H
+    // Lazy cloning: a path that takes over another path's history at an
+    // information leaf does not copy the pending arrays; it records the lane
+    // that holds them. src[log2 S]: lane holding this path's inputs of the
+    // running node of size S; bsrc[log2 H]: lane holding its beta[log2 H].
+    // Every path runs the same schedule, so no lane overwrites a pending
+    // array before the step that reads it fetches it.
+    int src[Log2<N>::v];
+    int bsrc[Log2<N>::v];
     long long pm;                  // path metric, units of 2^-19
 };
 
@@ -107,88 +115,123 @@ __device__ __forceinline__ int parent_llr(const int *ych, const PathState<N> &st
         return st.llr[S + k];
 }
 
+// A path continuing the history of lane par: for every node that is still
+// running (leaf I in its left half: inputs pending; in its right half: left
+// child's codeword pending) take over par's source lane.
 template <int N, int LW, int I, int S>
-__device__ __forceinline__ void clone_llr(PathState<N> &st, int par) {
+__device__ __forceinline__ void clone_src(PathState<N> &st, int par) {
     if constexpr (S <= N / 2) {
-        if constexpr ((I & (S / 2)) == 0) {
-#pragma unroll
-            for (int k = 0; k < S; ++k) st.llr[S + k] = __shfl_sync(kFull, st.llr[S + k], par, LW);
-        }
-        clone_llr<N, LW, I, S * 2>(st, par);
+        if constexpr ((I & (S / 2)) == 0) st.src[Log2<S>::v] = __shfl_sync(kFull, st.src[Log2<S>::v], par, LW);
+        clone_src<N, LW, I, S * 2>(st, par);
     }
 }
 
 template <int N, int LW, int I, int H>
-__device__ __forceinline__ void clone_beta(PathState<N> &st, int par) {
+__device__ __forceinline__ void clone_bsrc(PathState<N> &st, int par) {
     if constexpr (H <= N / 2) {
-        if constexpr ((I & H) != 0) st.beta[Log2<H>::v] = __shfl_sync(kFull, st.beta[Log2<H>::v], par, LW);
-        clone_beta<N, LW, I, H * 2>(st, par);
+        if constexpr ((I & H) != 0) st.bsrc[Log2<H>::v] = __shfl_sync(kFull, st.bsrc[Log2<H>::v], par, LW);
+        clone_bsrc<N, LW, I, H * 2>(st, par);
     }
+}
+
+// Whether leaves [OFF, OFF + LEN) hold an information leaf (always assumed for
+// a frozen set known only at run time).
+template <class FZ, int OFF, int LEN>
+__device__ __forceinline__ constexpr bool has_info() {
+    if constexpr (!FZ::kConst) {
+        return true;
+    } else if constexpr (LEN == 1) {
+        return !FZ::template frozen<OFF>();
+    } else {
+        return has_info<FZ, OFF, LEN / 2>() || has_info<FZ, OFF + LEN / 2, LEN / 2>();
+    }
+}
+
+// Outcome of the list step at an information leaf, for one lane.
+struct LeafStep {
+    long long pm;   // new path metric (kept lanes)
+    int par;        // lane whose history this lane continues
+    int count;      // new list size
+    unsigned bit;   // decided u of this lane's path
+};
+
+// The list step at an information leaf (it does not depend on which leaf, so
+// one copy of its code serves all of them): each of the |list| paths spawns
+// the children (u = HD, metric pm) and (u = 1 - HD, metric pm + |lam|); the
+// 2 |list| children are ranked by the key (metric, parent position, bit) and
+// the first min(2 |list|, L) are kept, child r going to lane r. Metrics are
+// taken relative to the frame's best path; when every relative metric of the
+// segment fits 25 bits the keys fit 32 bits (the usual case), otherwise the
+// same ranking runs on 64-bit keys.
+template <int LW>
+__device__ __noinline__ LeafStep list_step(int lam, long long pm, int lane, int count, int L,
+                                           unsigned long long *xchg) {
+    const unsigned hd = lam < 0 ? 1u : 0u;
+    const long long a = lam < 0 ? -(long long)lam : (long long)lam;
+    const bool valid = lane < count;
+    long long pmin = valid ? pm : 0x7fffffffffffffffLL;
+#pragma unroll
+    for (int o = LW / 2; o >= 1; o >>= 1) pmin = min(pmin, __shfl_xor_sync(kFull, pmin, o, LW));
+    const long long d0 = pm - pmin;
+    const bool small = !valid || d0 + a < (1LL << 25);
+    int r0 = 0, r1 = 0;
+    unsigned long long k0, k1;
+    if (__all_sync(kFull, small)) {
+        const uint32_t base32 = (uint32_t)lane << 1;
+        const uint32_t q0 = valid ? (((uint32_t)d0 << 6) | base32 | hd) : 0xffffffffu;
+        const uint32_t q1 = valid ? (((uint32_t)(d0 + a) << 6) | base32 | (hd ^ 1u)) : 0xffffffffu;
+#pragma unroll 4
+        for (int s = 0; s < LW; ++s) {
+            const uint32_t s0 = __shfl_sync(kFull, q0, s, LW);
+            const uint32_t s1 = __shfl_sync(kFull, q1, s, LW);
+            r0 += (s0 < q0) + (s1 < q0);
+            r1 += (s0 < q1) + (s1 < q1);
+        }
+        // back to absolute 64-bit keys for the exchange
+        k0 = valid ? ((((unsigned long long)pm) << 6) | (q0 & 63u)) : ~0ull;
+        k1 = valid ? ((((unsigned long long)(pm + a)) << 6) | (q1 & 63u)) : ~0ull;
+    } else {
+        const unsigned long long base = ((unsigned long long)lane << 1);
+        k0 = valid ? (((unsigned long long)pm << 6) | base | hd) : ~0ull;
+        k1 = valid ? (((unsigned long long)(pm + a) << 6) | base | (hd ^ 1u)) : ~0ull;
+#pragma unroll 4
+        for (int s = 0; s < LW; ++s) {
+            const unsigned long long s0 = __shfl_sync(kFull, k0, s, LW);
+            const unsigned long long s1 = __shfl_sync(kFull, k1, s, LW);
+            r0 += (s0 < k0) + (s1 < k0);
+            r1 += (s0 < k1) + (s1 < k1);
+        }
+    }
+    const int nc = min(2 * count, L);
+    if (r0 < nc) xchg[r0] = k0;
+    if (r1 < nc) xchg[r1] = k1;
+    __syncwarp();
+    const bool keep = lane < nc;
+    const unsigned long long kk = xchg[keep ? lane : 0];
+    __syncwarp();
+    LeafStep out;
+    out.par = keep ? (int)((kk >> 1) & 31ull) : lane;
+    out.pm = keep ? (long long)(kk >> 6) : pm;
+    out.count = nc;
+    out.bit = keep ? (unsigned)(kk & 1ull) : 0u;
+    return out;
 }
 
 template <int N, int LW, class FZ, int I>
 __device__ __forceinline__ uint64_t info_leaf(SclCtx<FZ> &cx, PathState<N> &st) {
     const int lam = st.llr[1];
-    const unsigned hd = lam < 0 ? 1u : 0u;
     if constexpr (LW == 1) {
         // one path: the child with the smaller key is always the hard decision
-        return hd;
+        return lam < 0 ? 1u : 0u;
     } else {
-        const long long a = lam < 0 ? -(long long)lam : (long long)lam;
-        const bool valid = cx.lane < cx.count;
-        // Rank of each child under the key (metric, parent position, bit). Metrics
-        // are taken relative to the frame's best path; when every relative
-        // metric of the warp fits 25 bits the keys fit 32 bits (the usual case),
-        // otherwise the same ranking runs on 64-bit keys.
-        long long pmin = valid ? st.pm : 0x7fffffffffffffffLL;
-#pragma unroll
-        for (int o = LW / 2; o >= 1; o >>= 1) pmin = min(pmin, __shfl_xor_sync(kFull, pmin, o, LW));
-        const long long d0 = st.pm - pmin;
-        const bool small = !valid || d0 + a < (1LL << 25);
-        int r0 = 0, r1 = 0;
-        unsigned long long k0, k1;
-        if (__all_sync(kFull, small)) {
-            const uint32_t base32 = (uint32_t)cx.lane << 1;
-            const uint32_t q0 = valid ? (((uint32_t)d0 << 6) | base32 | hd) : 0xffffffffu;
-            const uint32_t q1 = valid ? (((uint32_t)(d0 + a) << 6) | base32 | (hd ^ 1u)) : 0xffffffffu;
-#pragma unroll 4
-            for (int s = 0; s < LW; ++s) {
-                const uint32_t s0 = __shfl_sync(kFull, q0, s, LW);
-                const uint32_t s1 = __shfl_sync(kFull, q1, s, LW);
-                r0 += (s0 < q0) + (s1 < q0);
-                r1 += (s0 < q1) + (s1 < q1);
-            }
-            // back to absolute 64-bit keys for the exchange
-            k0 = valid ? ((((unsigned long long)st.pm) << 6) | (q0 & 63u)) : ~0ull;
-            k1 = valid ? ((((unsigned long long)(st.pm + a)) << 6) | (q1 & 63u)) : ~0ull;
-        } else {
-            const unsigned long long base = ((unsigned long long)cx.lane << 1);
-            k0 = valid ? (((unsigned long long)st.pm << 6) | base | hd) : ~0ull;
-            k1 = valid ? (((unsigned long long)(st.pm + a) << 6) | base | (hd ^ 1u)) : ~0ull;
-#pragma unroll 4
-            for (int s = 0; s < LW; ++s) {
-                const unsigned long long s0 = __shfl_sync(kFull, k0, s, LW);
-                const unsigned long long s1 = __shfl_sync(kFull, k1, s, LW);
-                r0 += (s0 < k0) + (s1 < k0);
-                r1 += (s0 < k1) + (s1 < k1);
-            }
-        }
-        const int nc = min(2 * cx.count, cx.L);
-        if (r0 < nc) cx.xchg[r0] = k0;
-        if (r1 < nc) cx.xchg[r1] = k1;
-        __syncwarp();
-        const bool keep = cx.lane < nc;
-        const unsigned long long kk = cx.xchg[keep ? cx.lane : 0];
-        __syncwarp();
-        const int par = keep ? (int)((kk >> 1) & 31ull) : cx.lane;
-        clone_llr<N, LW, I, 2>(st, par);
-        clone_beta<N, LW, I, 1>(st, par);
-        if (keep) st.pm = (long long)(kk >> 6);
-        cx.count = nc;
-        return keep ? (unsigned)(kk & 1ull) : 0u;
+        const LeafStep o = list_step<LW>(lam, st.pm, cx.lane, cx.count, cx.L, cx.xchg);
+        clone_src<N, LW, I, 2>(st, o.par);
+        clone_bsrc<N, LW, I, 1>(st, o.par);
+        st.pm = o.pm;
+        cx.count = o.count;
+        return o.bit;
     }
 }
-
 template <int N, int LW, class FZ, int I>
 __device__ __forceinline__ uint64_t leaf(SclCtx<FZ> &cx, PathState<N> &st) {
     bool frz;
@@ -212,19 +255,32 @@ __device__ __forceinline__ uint64_t node(SclCtx<FZ> &cx, PathState<N> &st) {
     } else {
         constexpr int H = S / 2;
         constexpr int LG = Log2<H>::v;
-        // a xor b on the left half: f
+        // a xor b on the left half: f (this node's inputs are still this lane's own)
 #pragma unroll
         for (int k = 0; k < H; ++k)
             st.llr[H + k] = minsum_f(parent_llr<N, S>(cx.ych, st, k), parent_llr<N, S>(cx.ych, st, k + H));
+        if constexpr (H > 1) st.src[Log2<H>::v] = cx.lane;
         st.beta[LG] = node<N, LW, FZ, H, OFF>(cx, st);
-        // b on the right half: g with the re-encoded left decisions
+        if constexpr (LW > 1) st.bsrc[LG] = cx.lane;
+        // b on the right half: g with the re-encoded left decisions; if the left
+        // half branched, this path's inputs now live in lane src
+        constexpr bool moved = LW > 1 && S < N && has_info<FZ, OFF, H>();
 #pragma unroll
         for (int k = 0; k < H; ++k) {
-            const int a = parent_llr<N, S>(cx.ych, st, k), b = parent_llr<N, S>(cx.ych, st, k + H);
+            int a, b;
+            if constexpr (moved) {
+                a = __shfl_sync(kFull, st.llr[S + k], st.src[Log2<S>::v], LW);
+                b = __shfl_sync(kFull, st.llr[S + k + H], st.src[Log2<S>::v], LW);
+            } else {
+                a = parent_llr<N, S>(cx.ych, st, k);
+                b = parent_llr<N, S>(cx.ych, st, k + H);
+            }
             st.llr[H + k] = ((st.beta[LG] >> k) & 1ull) ? b - a : b + a;
         }
+        if constexpr (H > 1) st.src[Log2<H>::v] = cx.lane;
         const uint64_t gr = node<N, LW, FZ, H, OFF + H>(cx, st);
-        const uint64_t be = st.beta[LG];
+        uint64_t be = st.beta[LG];
+        if constexpr (LW > 1 && has_info<FZ, OFF + H, H>()) be = __shfl_sync(kFull, be, st.bsrc[LG], LW);
         if constexpr (S <= 64) {
             return (be ^ gr) | (gr << (H & 63));
         } else {
