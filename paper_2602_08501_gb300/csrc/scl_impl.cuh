@@ -252,6 +252,19 @@ template <int N, int LW, class FZ, int S, int OFF>
 __device__ __forceinline__ uint64_t node(SclCtx<FZ> &cx, PathState<N> &st) {
     if constexpr (S == 1) {
         return leaf<N, LW, FZ, OFF>(cx, st);
+    } else if constexpr (S < N && !has_info<FZ, OFF, S>()) {
+        // all-frozen node: every leaf decides 0. With P(x) = max(0, -x) the
+        // min-sum updates satisfy P(f(a, b)) + P(a + b) = P(a) + P(b), so the
+        // leaves' metric increments add up to sum_k P(input_k) of this node
+        // (integers: exactly the leaf-by-leaf sum), and its codeword is 0
+        long long add = 0;
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            const int x = st.llr[S + k];
+            add += x < 0 ? -(long long)x : 0ll;
+        }
+        st.pm += add;
+        return 0;
     } else {
         constexpr int H = S / 2;
         constexpr int LG = Log2<H>::v;
