@@ -14,6 +14,8 @@
  *   - Hamming shells / code-weight sphere / translation ..... Sec. II-C, Eqs. (1)-(3)
  *   - stage 1: list decoding, CRC on the most reliable
  *     candidate, early termination .......................... Sec. III-A
+ *   - stage 1 alternative: ordered-statistics decoding
+ *     OSD(order) as the anchor list (the RM experiment) ..... Sec. IV-C
  *   - stage 2: MP-WSD update Eq. (4), Algorithm 1 with the
  *     top-m filter by the correlation gain of Eq. (5) and the
  *     exact-ED search, strict-improvement hop, final argmin ... Sec. III-B/C
@@ -546,6 +548,7 @@ typedef struct {
     const double *y;
     int64_t B;
     int L, J, rule, aom;
+    int osd_order;      /* < 0: SC-list stage 1; >= 0: OSD(osd_order) stage 1 */
     uint64_t *cw_out;   /* B x W */
     uint16_t *flags;    /* B */
     double *min_gap;    /* B, may be NULL */
@@ -554,6 +557,151 @@ typedef struct {
     int64_t next;       /* shared frame counter */
     pthread_mutex_t lock;
 } batch_job;
+
+/* ------------------------------------------------------------------------ */
+/* Stage 1 alternative: OSD(order) list (Sec. IV-C uses OSD(2) anchors)       */
+/* ------------------------------------------------------------------------ */
+/* The paper names OSD without details; this is the standard construction:
+ *  1. hard decisions hd_j = [y_j < 0] and reliabilities |y_j|;
+ *  2. positions in decreasing reliability, ties to the lower index;
+ *  3. the most reliable basis (MRB): walking the positions in that order, a
+ *     position joins when its generator column is independent of the ones
+ *     already chosen, until k are chosen. Gauss-Jordan on the generator makes
+ *     row t of G_sys the codeword that is 1 at the t-th chosen position and 0
+ *     at the other chosen ones (unique: the chosen columns are invertible);
+ *  4. c0 = XOR of the rows t with hd = 1 at the t-th chosen position (the
+ *     codeword that agrees with hd on the MRB);
+ *  5. candidates c0 XOR (rows of F) for every F with |F| <= order, enumerated
+ *     by |F|, then lexicographically;
+ *  6. discrepancy D(c) = sum_j |y_j| [c_j != hd_j]; ED(c) = ||y||^2 + n -
+ *     2 sum_j |y_j| + 4 D(c), so D orders candidates as ED does;
+ *  7. the list: the min(L, #candidates) smallest D, ties in enumeration order.
+ * Returns the list size; cw_list (L x n bytes) and d_list (L) hold it. */
+typedef struct {
+    double d;
+    int64_t idx;
+} osd_cand;
+
+static int osd_cmp(const void *pa, const void *pb) {
+    const osd_cand *a = (const osd_cand *)pa, *b = (const osd_cand *)pb;
+    if (a->d != b->d) return a->d < b->d ? -1 : 1;
+    return a->idx < b->idx ? -1 : (a->idx > b->idx ? 1 : 0);
+}
+
+typedef struct {
+    double r;
+    int j;
+} rel_pos;
+
+static int rel_cmp(const void *pa, const void *pb) {
+    const rel_pos *a = (const rel_pos *)pa, *b = (const rel_pos *)pb;
+    if (a->r != b->r) return a->r > b->r ? -1 : 1; /* more reliable first */
+    return a->j - b->j;
+}
+
+/* candidate number idx (enumeration order of step 5) -> its set F (ascending) */
+static int osd_subset(int64_t idx, int k, int order, int *F) {
+    for (int w = 0; w <= order && w <= k; w++) {
+        /* C(k, w) subsets of size w */
+        int64_t cnt = 1;
+        for (int t = 0; t < w; t++) cnt = cnt * (k - t) / (t + 1);
+        if (idx >= cnt) {
+            idx -= cnt;
+            continue;
+        }
+        /* the idx-th w-subset in lexicographic order */
+        int start = 0;
+        for (int t = 0; t < w; t++) {
+            for (int v = start; v < k; v++) {
+                int64_t rest = 1; /* C(k - v - 1, w - t - 1) */
+                for (int q = 0; q < w - t - 1; q++) rest = rest * (k - v - 1 - q) / (q + 1);
+                if (idx < rest) {
+                    F[t] = v;
+                    start = v + 1;
+                    break;
+                }
+                idx -= rest;
+            }
+        }
+        return w;
+    }
+    return -1;
+}
+
+int or_osd(const or_code *c, const double *y, int order, int L, uint8_t *cw_list, double *d_list) {
+    int n = c->n, k = c->k;
+    uint8_t hd[OR_MAXN];
+    rel_pos pos[OR_MAXN];
+    for (int j = 0; j < n; j++) {
+        hd[j] = y[j] < 0.0 ? 1 : 0;
+        pos[j].r = fabs(y[j]);
+        pos[j].j = j;
+    }
+    qsort(pos, (size_t)n, sizeof(rel_pos), rel_cmp);
+    /* generator rows (Arikan rows at the non-frozen indices) */
+    uint8_t *G = (uint8_t *)malloc((size_t)k * n);
+    for (int t = 0; t < k; t++)
+        for (int j = 0; j < n; j++) G[(size_t)t * n + j] = c->F[(size_t)c->info[t] * n + j];
+    int pivot_row[OR_MAXN], mrb[OR_MAXN], used[OR_MAXN];
+    for (int t = 0; t < k; t++) used[t] = 0;
+    int found = 0;
+    for (int q = 0; q < n && found < k; q++) {
+        int p = pos[q].j, r = -1;
+        for (int t = 0; t < k; t++)
+            if (!used[t] && G[(size_t)t * n + p]) {
+                r = t;
+                break;
+            }
+        if (r < 0) continue; /* column dependent on the chosen ones */
+        for (int t = 0; t < k; t++)
+            if (t != r && G[(size_t)t * n + p])
+                for (int j = 0; j < n; j++) G[(size_t)t * n + j] ^= G[(size_t)r * n + j];
+        used[r] = 1;
+        pivot_row[found] = r;
+        mrb[found] = p;
+        found++;
+    }
+    /* c0 */
+    uint8_t c0[OR_MAXN];
+    memset(c0, 0, (size_t)n);
+    for (int t = 0; t < found; t++)
+        if (hd[mrb[t]])
+            for (int j = 0; j < n; j++) c0[j] ^= G[(size_t)pivot_row[t] * n + j];
+    /* enumerate, score, keep the best */
+    int64_t ncand = 0;
+    for (int w = 0; w <= order && w <= found; w++) {
+        int64_t cnt = 1;
+        for (int t = 0; t < w; t++) cnt = cnt * (found - t) / (t + 1);
+        ncand += cnt;
+    }
+    osd_cand *cand = (osd_cand *)malloc(sizeof(osd_cand) * (size_t)ncand);
+    int F[OR_MAXN];
+    uint8_t cw[OR_MAXN];
+    for (int64_t i = 0; i < ncand; i++) {
+        int w = osd_subset(i, found, order, F);
+        memcpy(cw, c0, (size_t)n);
+        for (int t = 0; t < w; t++)
+            for (int j = 0; j < n; j++) cw[j] ^= G[(size_t)pivot_row[F[t]] * n + j];
+        double d = 0.0;
+        for (int j = 0; j < n; j++)
+            if (cw[j] != hd[j]) d += fabs(y[j]);
+        cand[i].d = d;
+        cand[i].idx = i;
+    }
+    qsort(cand, (size_t)ncand, sizeof(osd_cand), osd_cmp);
+    int count = (int)(ncand < L ? ncand : L);
+    for (int q = 0; q < count; q++) {
+        int w = osd_subset(cand[q].idx, found, order, F);
+        uint8_t *out = cw_list + (size_t)q * n;
+        memcpy(out, c0, (size_t)n);
+        for (int t = 0; t < w; t++)
+            for (int j = 0; j < n; j++) out[j] ^= G[(size_t)pivot_row[F[t]] * n + j];
+        if (d_list) d_list[q] = cand[q].d;
+    }
+    free(cand);
+    free(G);
+    return count;
+}
 
 static void pack_bits(const uint8_t *b, int n, uint64_t *w) {
     int W = (n + 63) / 64;
@@ -564,14 +712,20 @@ static void pack_bits(const uint8_t *b, int n, uint64_t *w) {
 
 /* Decode one frame. Flags: bit0 stage 2 ran, bit1 the output passes the CRC,
  * bits 4..7 outer iterations used by stage 2. */
-static void decode_frame(const or_code *c, const double *y, int L, int J, int rule, int aom, uint64_t *cw_out,
-                         uint16_t *flags, double *gap, uint8_t *anchors_out, int64_t *evals) {
+static void decode_frame(const or_code *c, const double *y, int L, int J, int rule, int aom, int osd_order,
+                         uint64_t *cw_out, uint16_t *flags, double *gap, uint8_t *anchors_out, int64_t *evals) {
     int n = c->n;
     uint8_t *ul = (uint8_t *)malloc((size_t)L * n);
     uint8_t *cl = (uint8_t *)malloc((size_t)L * n);
     double *pml = (double *)malloc(sizeof(double) * (size_t)L);
-    int count = or_scl(c, y, L, ul, pml);
-    for (int q = 0; q < count; q++) or_encode(c, ul + (size_t)q * n, cl + (size_t)q * n);
+    int count;
+    if (osd_order >= 0) {
+        /* stage 1 = OSD(osd_order): its list, best discrepancy first, are the anchors */
+        count = or_osd(c, y, osd_order, L, cl, pml);
+    } else {
+        count = or_scl(c, y, L, ul, pml);
+        for (int q = 0; q < count; q++) or_encode(c, ul + (size_t)q * n, cl + (size_t)q * n);
+    }
     if (anchors_out) {
         memset(anchors_out, 0, (size_t)L * n);
         memcpy(anchors_out, cl, (size_t)count * n);
@@ -618,7 +772,8 @@ static void *batch_worker(void *arg) {
         int64_t f = jb->next++;
         pthread_mutex_unlock(&jb->lock);
         if (f >= jb->B) break;
-        decode_frame(jb->c, jb->y + f * n, jb->L, jb->J, jb->rule, jb->aom, jb->cw_out + f * W, jb->flags + f,
+        decode_frame(jb->c, jb->y + f * n, jb->L, jb->J, jb->rule, jb->aom, jb->osd_order, jb->cw_out + f * W,
+                     jb->flags + f,
                      jb->min_gap ? jb->min_gap + f : NULL,
                      jb->anchors_out ? jb->anchors_out + (size_t)f * jb->L * n : NULL,
                      jb->evals ? jb->evals + f : NULL);
@@ -628,12 +783,13 @@ static void *batch_worker(void *arg) {
 
 /* Decode B frames (y: B x n FP64). Outputs as described above. nthreads <= 0
  * means 1. Returns 0, or -1 on bad arguments. */
-int or_decode(const or_code *c, const double *y, int64_t B, int L, int J, int rule, int aom, int nthreads,
-              uint64_t *cw_out, uint16_t *flags, double *min_gap, uint8_t *anchors_out, int64_t *evals) {
+int or_decode(const or_code *c, const double *y, int64_t B, int L, int J, int rule, int aom, int osd_order,
+              int nthreads, uint64_t *cw_out, uint16_t *flags, double *min_gap, uint8_t *anchors_out,
+              int64_t *evals) {
     if (!c || L < 1 || J < 0 || B < 0) return -1;
     if (B == 0) return 0;
     batch_job jb;
-    jb.c = c; jb.y = y; jb.B = B; jb.L = L; jb.J = J; jb.rule = rule; jb.aom = aom;
+    jb.c = c; jb.y = y; jb.B = B; jb.L = L; jb.J = J; jb.rule = rule; jb.aom = aom; jb.osd_order = osd_order;
     jb.cw_out = cw_out; jb.flags = flags; jb.min_gap = min_gap; jb.anchors_out = anchors_out; jb.evals = evals;
     jb.next = 0;
     pthread_mutex_init(&jb.lock, NULL);
