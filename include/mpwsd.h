@@ -71,6 +71,11 @@ extern "C" {
 #define MPWSD_RULE_TOP1 0       /* stage 1 succeeds iff the best-metric list entry passes the CRC (Sec. III-A) */
 #define MPWSD_RULE_ANY 1        /* stage 1 succeeds with the best-metric entry that passes the CRC */
 
+#define MPWSD_STAGE1_SCL 0      /* stage 1 = min-sum SC-list decoding (Sec. III-A) */
+#define MPWSD_STAGE1_OSD 1      /* stage 1 = ordered-statistics decoding OSD(osd_order), the anchors of the RM
+                                   experiment (Sec. IV-C); needs k <= 32 */
+#define MPWSD_MAX_OSD_ORDER 4
+
 /* Output flag bits (one uint16 per frame). */
 #define MPWSD_FLAG_STAGE2 0x0001u   /* stage 2 ran for this frame */
 #define MPWSD_FLAG_CRC_OK 0x0002u   /* the output codeword passes the CRC */
@@ -86,7 +91,9 @@ typedef struct mpwsd_opts {
                         given (workspace, buffers, B, L, T, options) captures it (on a private stream,
                         without running it) and later identical calls replay it; the handle keeps up to
                         256 graphs. Same results as without. */
-    int reserved[4]; /* must be zero */
+    int stage1;      /* MPWSD_STAGE1_SCL (default) or MPWSD_STAGE1_OSD */
+    int osd_order;   /* OSD reprocessing order, 0..MPWSD_MAX_OSD_ORDER (MPWSD_STAGE1_OSD only) */
+    int reserved[2]; /* must be zero */
 } mpwsd_opts;
 
 /* Counters accumulated on the device by every decode of a code handle since
@@ -230,6 +237,24 @@ MPWSD_API int mpwsd_stage1_list(mpwsd_code *code, const float *y_dev, int64_t B,
                       int64_t *list_pm_dev, void *stream);
 
 /*
+ * mpwsd_osd_list -- the OSD(order) stage 1 alone: the list of the min(L, #candidates)
+ * candidates of smallest discrepancy D(c) = sum_j |y_j| [c_j != hd_j] (ED order;
+ * ties in the enumeration order), for B frames. Construction: hard decisions
+ * hd_j = [y_j < 0]; the most reliable basis (positions by decreasing |y|, ties
+ * to the lower index, kept when independent of those before); the codeword
+ * that agrees with hd on it, and every codeword that differs from it on at most
+ * `order` of the basis positions, enumerated by the number of flips, then
+ * lexicographically by basis rank.
+ *
+ *   list_cw_dev  device, B x L x W uint64 codewords.
+ *   list_d_dev   device, B x L int64: D in units of 2^-19.
+ * Entries past the list size are not written. Needs k <= 32, 0 <= order <=
+ * MPWSD_MAX_OSD_ORDER, 1 <= L <= MPWSD_MAX_L. Asynchronous.
+ */
+MPWSD_API int mpwsd_osd_list(mpwsd_code *code, const float *y_dev, int64_t B, int order, int L, uint64_t *list_cw_dev,
+                             int64_t *list_d_dev, void *stream);
+
+/*
  * mpwsd_score_topk -- the scoring step of stage 2 alone: for each row r,
  * the trajectory centre c_r (frame frame_dev[r] of y_dev) gets the scores
  * S(r, p) = sum_{j in supp p} y_j x_j(c_r) for every pattern p (-G/2 of
@@ -261,7 +286,8 @@ MPWSD_API int mpwsd_sync(mpwsd_code *code, void *stream);
 #define MPWSD_KERNEL_HOP 3        /* FP64 near-tie re-rank + hop + compaction */
 #define MPWSD_KERNEL_RESCAN 4     /* full FP64 rescan of overflowing rows */
 #define MPWSD_KERNEL_FINAL 5      /* per-frame argmin ED + flags */
-#define MPWSD_KERNEL_KINDS 6
+#define MPWSD_KERNEL_OSD 6        /* stage 1 by OSD(order) + CRC + compaction */
+#define MPWSD_KERNEL_KINDS 7
 
 typedef struct mpwsd_kernel_time {
     int64_t launches; /* kernels of this class launched while profiling */

@@ -82,6 +82,7 @@ struct CodeDev {
     uint16_t *pat_tiles = nullptr;  // tiles of tc_patterns_per_tile(n) x n bf16, smem image (128B swizzle, K-major)
     int64_t n_tiles = 0;
     uint64_t *crc_masks = nullptr;  // crc_len x W, codeword domain: syndrome bit b = parity(c & mask_b)
+    uint64_t *gen_rows = nullptr;   // k x W: generator rows (Arikan rows at the non-frozen indices, ascending)
     DevStats *stats = nullptr;
     int num_sms = 0;
     // Bounded device waits: a wait that exceeds this records an error and the
@@ -110,6 +111,22 @@ struct SclArgs {
     int64_t *list_pm;
 };
 
+struct OsdArgs {
+    const float *y;
+    int64_t B;
+    int L;
+    int order;
+    int mode;            // 0 = decode (CRC + compaction), 1 = list output
+    int rule;            // MPWSD_RULE_*
+    int use_crc;
+    int write_yhl;
+    uint64_t *cw_out;
+    uint16_t *flags_out;
+    Workspace ws;
+    uint64_t *list_cw;
+    int64_t *list_d;
+};
+
 struct ScoreArgs {
     const float *y;
     const int *rows;          // active list: trajectory ids (decode) or row ids (direct)
@@ -135,6 +152,7 @@ struct ScoreArgs {
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_scl(const CodeDev &c, const SclArgs &a, cudaStream_t s);
+cudaError_t launch_osd(const CodeDev &c, const OsdArgs &a, cudaStream_t s);
 cudaError_t launch_score_fp32(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
 cudaError_t launch_score_tc(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
 // y (B x n) -> bf16 hi / lo words and ||y||_1 per frame, for direct-mode tensor-core scoring

@@ -90,10 +90,11 @@ struct mpwsd_code {
     struct GraphKey {
         const void *ws, *y, *cw, *fl;
         int64_t ws_B, B;  // workspace layout (base, max_B, max_L) and the call
-        int ws_L, L, T, mode, rule, aom;
+        int ws_L, L, T, mode, rule, aom, stage1, osd_order;
         bool operator==(const GraphKey &o) const {
             return ws == o.ws && ws_B == o.ws_B && ws_L == o.ws_L && y == o.y && cw == o.cw && fl == o.fl &&
-                   B == o.B && L == o.L && T == o.T && mode == o.mode && rule == o.rule && aom == o.aom;
+                   B == o.B && L == o.L && T == o.T && mode == o.mode && rule == o.rule && aom == o.aom &&
+                   stage1 == o.stage1 && osd_order == o.osd_order;
         }
     };
     struct GraphEnt {
@@ -157,11 +158,13 @@ static void free_code_device(CodeDev &d) {
     cudaFree(d.pat_supp);
     cudaFree(d.pat_tiles);
     cudaFree(d.crc_masks);
+    cudaFree(d.gen_rows);
     cudaFree(d.stats);
     d.pat_bits = nullptr;
     d.pat_supp = nullptr;
     d.pat_tiles = nullptr;
     d.crc_masks = nullptr;
+    d.gen_rows = nullptr;
     d.stats = nullptr;
 }
 
@@ -325,6 +328,11 @@ extern "C" int mpwsd_load_code(int n, const uint8_t *G, const uint8_t *frozen, i
             if (par) masks[(size_t)b * W + j / 64] |= 1ull << (j % 64);
         }
     }
+    // generator rows for OSD: row t = row info[t] of the Arikan kernel power
+    std::vector<uint64_t> gen((size_t)k * W, 0);
+    for (int t = 0; t < k; ++t)
+        for (int j = 0; j < n; ++j)
+            if (kron_entry(info[t], j)) gen[(size_t)t * W + j / 64] |= 1ull << (j % 64);
     // device images
     struct Up {
         void **dst;
@@ -335,6 +343,7 @@ extern "C" int mpwsd_load_code(int n, const uint8_t *G, const uint8_t *frozen, i
         {(void **)&d.pat_supp, supp.data(), supp.size() * 4},
         {(void **)&d.pat_tiles, tiles.data(), tiles.size() * 2},
         {(void **)&d.crc_masks, masks.data(), masks.size() * 8},
+        {(void **)&d.gen_rows, gen.data(), gen.size() * 8},
     };
     for (auto &u : ups) {
         e = dev_alloc(u.dst, u.bytes);
@@ -482,7 +491,13 @@ static int check_opts(const mpwsd_opts *opts, mpwsd_opts *o) {
         return fail(MPWSD_EINVAL, "score_mode = %d", o->score_mode);
     if (o->stage1_rule != MPWSD_RULE_TOP1 && o->stage1_rule != MPWSD_RULE_ANY)
         return fail(MPWSD_EINVAL, "stage1_rule = %d", o->stage1_rule);
-    for (int i = 0; i < 4; ++i)
+    if (o->stage1 != MPWSD_STAGE1_SCL && o->stage1 != MPWSD_STAGE1_OSD)
+        return fail(MPWSD_EINVAL, "stage1 = %d", o->stage1);
+    if (o->stage1 == MPWSD_STAGE1_OSD && (o->osd_order < 0 || o->osd_order > MPWSD_MAX_OSD_ORDER))
+        return fail(MPWSD_EINVAL, "osd_order = %d: must be 0..%d", o->osd_order, MPWSD_MAX_OSD_ORDER);
+    if (o->stage1 == MPWSD_STAGE1_SCL && o->osd_order != 0)
+        return fail(MPWSD_EINVAL, "osd_order is for MPWSD_STAGE1_OSD");
+    for (int i = 0; i < 2; ++i)
         if (o->reserved[i]) return fail(MPWSD_EINVAL, "reserved option fields must be zero");
     return MPWSD_OK;
 }
@@ -506,18 +521,34 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
     CodeDev &d = code->d;
     cudaError_t e = cudaMemsetAsync(ws.counters, 0, 64 * sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    SclArgs sa{};
-    sa.y = y_dev;
-    sa.B = B;
-    sa.L = L;
-    sa.mode = 0;
-    sa.rule = o.stage1_rule;
-    sa.use_crc = d.crc_len > 0 && !o.always_on;
-    sa.cw_out = cw_dev;
-    sa.flags_out = flags_dev;
-    sa.ws = ws;
-    sa.write_yhl = o.score_mode == MPWSD_SCORE_BF16X2;
-    e = timed_launch(code, MPWSD_KERNEL_SCL, s, [&] { return launch_scl(d, sa, s); });
+    if (o.stage1 == MPWSD_STAGE1_OSD) {
+        OsdArgs oa{};
+        oa.y = y_dev;
+        oa.B = B;
+        oa.L = L;
+        oa.order = o.osd_order;
+        oa.mode = 0;
+        oa.rule = o.stage1_rule;
+        oa.use_crc = d.crc_len > 0 && !o.always_on;
+        oa.write_yhl = o.score_mode == MPWSD_SCORE_BF16X2;
+        oa.cw_out = cw_dev;
+        oa.flags_out = flags_dev;
+        oa.ws = ws;
+        e = timed_launch(code, MPWSD_KERNEL_OSD, s, [&] { return launch_osd(d, oa, s); });
+    } else {
+        SclArgs sa{};
+        sa.y = y_dev;
+        sa.B = B;
+        sa.L = L;
+        sa.mode = 0;
+        sa.rule = o.stage1_rule;
+        sa.use_crc = d.crc_len > 0 && !o.always_on;
+        sa.cw_out = cw_dev;
+        sa.flags_out = flags_dev;
+        sa.ws = ws;
+        sa.write_yhl = o.score_mode == MPWSD_SCORE_BF16X2;
+        e = timed_launch(code, MPWSD_KERNEL_SCL, s, [&] { return launch_scl(d, sa, s); });
+    }
     if (e != cudaSuccess) return cuda_fail(e, "stage-1 launch");
     for (int it = 0; it < T; ++it) {
         ScoreArgs a{};
@@ -553,7 +584,8 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
 static int decode_graph(mpwsd_code *code, Workspace &ws, const float *y_dev, int64_t B, int L, int T,
                         const mpwsd_opts &o, uint64_t *cw_dev, uint16_t *flags_dev, cudaStream_t s) {
     mpwsd_code::GraphKey key{ws.base,  y_dev, cw_dev, flags_dev,     ws.max_B,      B,
-                             ws.max_L, L,     T,      o.score_mode, o.stage1_rule, o.always_on};
+                             ws.max_L, L,     T,      o.score_mode, o.stage1_rule, o.always_on,
+                             o.stage1, o.osd_order};
     std::lock_guard<std::mutex> lk(code->mu);
     for (auto &g : code->graphs)
         if (g.key == key) {
@@ -613,6 +645,8 @@ static int check_decode_args(mpwsd_code *code, const float *y_dev, int64_t B, in
     if (st) return st;
     if (o->score_mode == MPWSD_SCORE_BF16X2 && !score_tc_supported(code->d))
         return fail(MPWSD_EUNSUPPORTED, "BF16X2 tensor-core scoring needs n = 64 or 128");
+    if (o->stage1 == MPWSD_STAGE1_OSD && code->d.k > 32)
+        return fail(MPWSD_EUNSUPPORTED, "OSD stage 1 needs k <= 32 (k = %d)", code->d.k);
     return check_device(code);
 }
 
@@ -676,6 +710,29 @@ extern "C" int mpwsd_stage1_list(mpwsd_code *code, const float *y_dev, int64_t B
     cudaError_t e = timed_launch(code, MPWSD_KERNEL_SCL, (cudaStream_t)stream,
                                  [&] { return launch_scl(code->d, sa, (cudaStream_t)stream); });
     if (e != cudaSuccess) return cuda_fail(e, "stage-1 launch");
+    return MPWSD_OK;
+}
+
+extern "C" int mpwsd_osd_list(mpwsd_code *code, const float *y_dev, int64_t B, int order, int L, uint64_t *list_cw_dev,
+                              int64_t *list_d_dev, void *stream) {
+    if (!code) return fail(MPWSD_EINVAL, "code is NULL");
+    if (B < 0 || L < 1 || L > MPWSD_MAX_L) return fail(MPWSD_EINVAL, "need B >= 0 and 1 <= L <= 32");
+    if (order < 0 || order > MPWSD_MAX_OSD_ORDER) return fail(MPWSD_EINVAL, "order = %d: must be 0..%d", order,
+                                                              MPWSD_MAX_OSD_ORDER);
+    if (code->d.k > 32) return fail(MPWSD_EUNSUPPORTED, "OSD needs k <= 32 (k = %d)", code->d.k);
+    if (B > 0 && (!y_dev || !list_cw_dev || !list_d_dev)) return fail(MPWSD_EINVAL, "NULL buffer");
+    if (B == 0) return MPWSD_OK;
+    OsdArgs oa{};
+    oa.y = y_dev;
+    oa.B = B;
+    oa.L = L;
+    oa.order = order;
+    oa.mode = 1;
+    oa.list_cw = list_cw_dev;
+    oa.list_d = list_d_dev;
+    cudaError_t e = timed_launch(code, MPWSD_KERNEL_OSD, (cudaStream_t)stream,
+                                 [&] { return launch_osd(code->d, oa, (cudaStream_t)stream); });
+    if (e != cudaSuccess) return cuda_fail(e, "OSD launch");
     return MPWSD_OK;
 }
 

@@ -21,6 +21,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "mpwsd.h")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 SCORE_BF16X2, SCORE_FP32 = 0, 1
 RULE_TOP1, RULE_ANY = 0, 1
+STAGE1_SCL, STAGE1_OSD = 0, 1
 FLAG_STAGE2, FLAG_CRC_OK, FLAG_RESCAN, FLAG_ERROR = 0x1, 0x2, 0x4, 0x100
 ITERS_SHIFT = 4
 MAX_L, MAX_T, TOPK = 32, 15, 4
@@ -38,14 +39,15 @@ class MpwsdError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("score_mode", ctypes.c_int), ("stage1_rule", ctypes.c_int), ("always_on", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("use_graph", ctypes.c_int), ("stage1", ctypes.c_int), ("osd_order", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class _KTime(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 
-KERNEL_NAMES = ("scl", "score_tc", "score_fp32", "hop", "rescan", "final")
+KERNEL_NAMES = ("scl", "score_tc", "score_fp32", "hop", "rescan", "final", "osd")
 
 
 class _Stats(ctypes.Structure):
@@ -82,6 +84,7 @@ def lib():
             "mpwsd_workspace_bytes": (i32, [P, i64, i32, ctypes.POINTER(ctypes.c_size_t)]),
             "mpwsd_decode_ws": (i32, [P, P, P, i64, i32, i32, P, P, P, P]),
             "mpwsd_stage1_list": (i32, [P, P, i64, i32, P, P, P]),
+            "mpwsd_osd_list": (i32, [P, P, i64, i32, i32, P, P, P]),
             "mpwsd_score_topk": (i32, [P, i32, P, i64, P, P, i64, P, P, P]),
             "mpwsd_sync": (i32, [P, P]),
             "mpwsd_stats_get": (i32, [P, ctypes.POINTER(_Stats)]),
@@ -205,18 +208,22 @@ class Code:
             pass
 
     @staticmethod
-    def _opts(score_mode, rule, always_on, use_graph=False):
+    def _opts(score_mode, rule, always_on, use_graph=False, osd_order=None):
         o = _Opts()
         o.score_mode = {"bf16x2": SCORE_BF16X2, "fp32": SCORE_FP32}.get(score_mode, score_mode)
         o.stage1_rule = {"top1": RULE_TOP1, "any": RULE_ANY}.get(rule, rule)
         o.always_on = int(bool(always_on))
         o.use_graph = int(bool(use_graph))
+        o.stage1 = STAGE1_SCL if osd_order is None else STAGE1_OSD
+        o.osd_order = 0 if osd_order is None else int(osd_order)
         return o
 
     def decode(self, y, L: int, T: int, score_mode="bf16x2", rule="top1", always_on=False, cw_out=None,
-               flags_out=None, stream=None, workspace: Workspace | None = None, use_graph: bool = False):
+               flags_out=None, stream=None, workspace: Workspace | None = None, use_graph: bool = False,
+               osd_order: int | None = None):
         """Two-stage decode of y (B x n float32 CUDA tensor). Returns (cw, flags)
-        as CUDA tensors (B x W int64 bit patterns, B int16); asynchronous."""
+        as CUDA tensors (B x W int64 bit patterns, B int16); asynchronous.
+        Stage 1 is SC-list, or OSD(osd_order) when osd_order is given."""
         import torch
 
         B = int(y.shape[0]) if y.dim() == 2 else 0
@@ -226,7 +233,7 @@ class Code:
             cw_out = torch.empty((B, self.W), dtype=torch.int64, device=y.device)
         if flags_out is None:
             flags_out = torch.empty((B,), dtype=torch.int16, device=y.device)
-        o = self._opts(score_mode, rule, always_on, use_graph)
+        o = self._opts(score_mode, rule, always_on, use_graph, osd_order)
         args = (_dev(y, torch.float32, "y"), B, int(L), int(T), ctypes.byref(o), _dev(cw_out, torch.int64, "cw_out"),
                 _dev(flags_out, torch.int16, "flags_out"), _stream_ptr(stream))
         if workspace is None:
@@ -244,6 +251,19 @@ class Code:
         _check(lib().mpwsd_stage1_list(self._h, _dev(y, torch.float32, "y"), B, int(L), _dev(cw, torch.int64, "cw"),
                                        _dev(pm, torch.int64, "pm"), _stream_ptr(stream)), "stage1_list")
         return cw, pm
+
+    def osd_list(self, y, order: int, L: int, stream=None):
+        """OSD(order) list of every frame: (cw B x L x W int64, D B x L int64 in units of
+        2^-19; entries past the list size keep D = -1)."""
+        import torch
+
+        B = int(y.shape[0])
+        cw = torch.zeros((B, L, self.W), dtype=torch.int64, device=y.device)
+        d = torch.full((B, L), -1, dtype=torch.int64, device=y.device)
+        _check(lib().mpwsd_osd_list(self._h, _dev(y, torch.float32, "y"), B, int(order), int(L),
+                                    _dev(cw, torch.int64, "cw"), _dev(d, torch.int64, "d"), _stream_ptr(stream)),
+               "osd_list")
+        return cw, d
 
     def score_topk(self, y, frame, cw, score_mode="bf16x2", stream=None):
         import torch
