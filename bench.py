@@ -40,6 +40,9 @@ WORKLOADS = {
     "rm27_crc6_1p5db": dict(code="rm27_crc6", m=7, r=2, ebn0=1.5, frames=1_000_000, seed=2, L=16, T=6,
                             weights=[32], desc="RM(2,7)+CRC-6, Eb/N0 1.5 dB, 1e6 frames, seed 2, L=16, T=6, "
                                                "10668 w32 patterns"),
+    "rm27_crc6_osd2": dict(code="rm27_crc6", m=7, r=2, ebn0=1.5, frames=1_000_000, seed=2, L=16, T=6,
+                           weights=[32], osd=2, desc="RM(2,7)+CRC-6, Eb/N0 1.5 dB, 1e6 frames, seed 2, OSD(2) "
+                                                     "stage 1, L=16, T=6, 10668 w32 patterns"),
     "rm26_crc6_l32": dict(code="rm26_crc6", m=6, r=2, ebn0=0.5, frames=200_000, seed=3, L=32, T=8,
                           weights=[16, 24], desc="RM(2,6)+CRC-6, Eb/N0 0.5 dB, 2e5 frames, seed 3, L=32, T=8, "
                                                  "294252 w16+w24 patterns"),
@@ -189,7 +192,7 @@ def oracle_decode(wl_cfg, y, threads):
 
     code = oracle.rm_code(wl_cfg["m"], wl_cfg["r"], crc_poly=0x21, crc_len=6)
     code = code.with_patterns(code.enumerate_codewords(wl_cfg["weights"]))
-    return code, code.decode(y, wl_cfg["L"], wl_cfg["T"], threads=threads)
+    return code, code.decode(y, wl_cfg["L"], wl_cfg["T"], threads=threads, osd_order=wl_cfg.get("osd"))
 
 
 def time_oracle(wl_cfg, seconds: float, threads: int):
@@ -200,12 +203,12 @@ def time_oracle(wl_cfg, seconds: float, threads: int):
     probe = synth.make_workload(wl_cfg["code"], wl_cfg["ebn0"], 2000, seed=wl_cfg["seed"])
     code, _ = oracle_decode(wl_cfg, probe.y[:200], threads)  # builds the oracle and its pattern set
     t = time.perf_counter()
-    code.decode(probe.y, wl_cfg["L"], wl_cfg["T"], threads=threads)
+    code.decode(probe.y, wl_cfg["L"], wl_cfg["T"], threads=threads, osd_order=wl_cfg.get("osd"))
     rate = probe.B / max(time.perf_counter() - t, 1e-6)
     n = int(min(max(2000, rate * seconds), wl_cfg["frames"]))
     wl = synth.make_workload(wl_cfg["code"], wl_cfg["ebn0"], n, seed=wl_cfg["seed"])
     t = time.perf_counter()
-    out = code.decode(wl.y, wl_cfg["L"], wl_cfg["T"], threads=threads)
+    out = code.decode(wl.y, wl_cfg["L"], wl_cfg["T"], threads=threads, osd_order=wl_cfg.get("osd"))
     dt = time.perf_counter() - t
     return wl, out, dt
 
@@ -223,16 +226,16 @@ def run_reference(args, wl_cfg):
     probe = synth.make_workload(wl_cfg["code"], wl_cfg["ebn0"], 1000, seed=wl_cfg["seed"])
     code, _ = oracle_decode(wl_cfg, probe.y[:100], threads)
     t = time.perf_counter()
-    code.decode(probe.y, wl_cfg["L"], wl_cfg["T"], threads=threads)
+    code.decode(probe.y, wl_cfg["L"], wl_cfg["T"], threads=threads, osd_order=wl_cfg.get("osd"))
     rate = probe.B / max(time.perf_counter() - t, 1e-6)
     per_step = int(min(max(1000, rate * args.ref_step_seconds), wl_cfg["frames"]))
     wl = synth.make_workload(wl_cfg["code"], wl_cfg["ebn0"], per_step, seed=wl_cfg["seed"])
     for _ in range(args.warmup):
-        code.decode(wl.y[:min(per_step, 500)], wl_cfg["L"], wl_cfg["T"], threads=threads)
+        code.decode(wl.y[:min(per_step, 500)], wl_cfg["L"], wl_cfg["T"], threads=threads, osd_order=wl_cfg.get("osd"))
     times = []
     for _ in range(args.steps):
         t = time.perf_counter()
-        code.decode(wl.y, wl_cfg["L"], wl_cfg["T"], threads=threads)
+        code.decode(wl.y, wl_cfg["L"], wl_cfg["T"], threads=threads, osd_order=wl_cfg.get("osd"))
         times.append(time.perf_counter() - t)
     total = sum(times)
     value = per_step * args.steps / total
@@ -285,7 +288,7 @@ def run_ours(args, wl_cfg):
     stream = torch.cuda.current_stream()
 
     def step():
-        code.decode(y_dev, L, T, score_mode=args.mode, cw_out=cw_dev, flags_out=fl_dev)
+        code.decode(y_dev, L, T, score_mode=args.mode, cw_out=cw_dev, flags_out=fl_dev, osd_order=wl_cfg.get("osd"))
 
     for _ in range(args.warmup):
         step()
@@ -321,7 +324,7 @@ def run_ours(args, wl_cfg):
 
     def e2e_step():
         y_dev.copy_(y_host, non_blocking=True)
-        code.decode(y_dev, L, T, score_mode=args.mode, cw_out=cw_dev, flags_out=fl_dev)
+        code.decode(y_dev, L, T, score_mode=args.mode, cw_out=cw_dev, flags_out=fl_dev, osd_order=wl_cfg.get("osd"))
         cw_host.copy_(cw_dev, non_blocking=True)
         fl_host.copy_(fl_dev, non_blocking=True)
 
@@ -392,6 +395,16 @@ def run_ours(args, wl_cfg):
             return {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "Top/s",
                     "frac": ach / (alu_peak / 1e12), "traffic": tr, "kernel": "scl",
                     "peak_kind": "152 SMs x 128 INT32 lanes x max SM clock", "ops_per_launch": ops}
+        if kname == "osd":
+            # per frame: the discrepancy of every candidate (n weighted adds each) and the elimination (n k)
+            kk = int(code.k)
+            order = int(wl_cfg.get("osd", 0))
+            ncand = sum(math.comb(kk, w) for w in range(order + 1))
+            ops = frames * n * (ncand + kk) / launches
+            ach = ops / per_launch_s / 1e12
+            return {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "Top/s",
+                    "frac": ach / (alu_peak / 1e12), "traffic": None, "kernel": "osd",
+                    "peak_kind": "152 SMs x 128 INT32 lanes x max SM clock", "ops_per_launch": ops}
         if kname == "hop":
             # bytes a row needs: its list entry (4 + 32), centre, D, state, 1/L of its frame's y row and
             # slot data, the supports of its candidates, and on a hop the written centre, D, state, entry
@@ -413,7 +426,7 @@ def run_ours(args, wl_cfg):
                 "kernel": kname}
 
     roof = roofline_for(dominant)
-    others = [roofline_for(k) for k in ("scl", "score_tc", "score_fp32", "hop") if k in kinds and k != dominant]
+    others = [roofline_for(k) for k in ("scl", "osd", "score_tc", "score_fp32", "hop") if k in kinds and k != dominant]
 
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,

@@ -183,6 +183,7 @@ class Code:
                                      ctypes.byref(h)), "load_code")
         self._h = h
         self.k_info, self.crc_poly, self.crc_len = int(k_info), int(crc_poly), int(crc_len)
+        self.k = int((self.frozen == 0).sum())
 
     @classmethod
     def rm(cls, m: int, r: int, crc_poly: int = 0, crc_len: int = 0, weights=None, patterns=None) -> "Code":
