@@ -83,6 +83,9 @@ struct CodeDev {
     int64_t n_tiles = 0;
     uint64_t *crc_masks = nullptr;  // crc_len x W, codeword domain: syndrome bit b = parity(c & mask_b)
     uint64_t *gen_rows = nullptr;   // k x W: generator rows (Arikan rows at the non-frozen indices, ascending)
+    // OSD row sets of at most kOsdMaxOrder rows in candidate-number order (by size, then
+    // lexicographic): rows at 5 bits each from bit 0, the size in bits 20..22; k <= 32 only
+    uint32_t *osd_sets = nullptr;
     DevStats *stats = nullptr;
     int num_sms = 0;
     // Bounded device waits: a wait that exceeds this records an error and the
@@ -116,6 +119,7 @@ struct OsdArgs {
     int64_t B;
     int L;
     int order;
+    int ncand;           // osd_candidates(k, order)
     int mode;            // 0 = decode (CRC + compaction), 1 = list output
     int rule;            // MPWSD_RULE_*
     int use_crc;
@@ -152,6 +156,16 @@ struct ScoreArgs {
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_scl(const CodeDev &c, const SclArgs &a, cudaStream_t s);
+constexpr int kOsdMaxOrder = 4;
+// number of OSD(order) candidates: sum_{w <= order} C(k, w)
+inline int osd_candidates(int k, int order) {
+    long long tot = 0, cw = 1;
+    for (int w = 0; w <= order && w <= k; ++w) {
+        tot += cw;
+        cw = cw * (k - w) / (w + 1);
+    }
+    return (int)tot;
+}
 cudaError_t launch_osd(const CodeDev &c, const OsdArgs &a, cudaStream_t s);
 cudaError_t launch_score_fp32(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
 cudaError_t launch_score_tc(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);

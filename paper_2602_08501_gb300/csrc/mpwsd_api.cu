@@ -159,12 +159,14 @@ static void free_code_device(CodeDev &d) {
     cudaFree(d.pat_tiles);
     cudaFree(d.crc_masks);
     cudaFree(d.gen_rows);
+    cudaFree(d.osd_sets);
     cudaFree(d.stats);
     d.pat_bits = nullptr;
     d.pat_supp = nullptr;
     d.pat_tiles = nullptr;
     d.crc_masks = nullptr;
     d.gen_rows = nullptr;
+    d.osd_sets = nullptr;
     d.stats = nullptr;
 }
 
@@ -333,6 +335,25 @@ extern "C" int mpwsd_load_code(int n, const uint8_t *G, const uint8_t *frozen, i
     for (int t = 0; t < k; ++t)
         for (int j = 0; j < n; ++j)
             if (kron_entry(info[t], j)) gen[(size_t)t * W + j / 64] |= 1ull << (j % 64);
+    // OSD candidate row sets in number order: by size, then lexicographic (k <= 32 only)
+    std::vector<uint32_t> osd_sets;
+    if (k <= 32) {
+        osd_sets.reserve((size_t)osd_candidates(k, kOsdMaxOrder));
+        for (int w = 0; w <= kOsdMaxOrder && w <= k; ++w) {
+            int sel[kOsdMaxOrder];
+            for (int t = 0; t < w; ++t) sel[t] = t;
+            for (;;) {
+                uint32_t v = (uint32_t)w << 20;
+                for (int t = 0; t < w; ++t) v |= (uint32_t)sel[t] << (5 * t);
+                osd_sets.push_back(v);
+                int t = w - 1;  // next w-subset in lexicographic order
+                while (t >= 0 && sel[t] == k - w + t) --t;
+                if (t < 0) break;
+                ++sel[t];
+                for (int u = t + 1; u < w; ++u) sel[u] = sel[u - 1] + 1;
+            }
+        }
+    }
     // device images
     struct Up {
         void **dst;
@@ -344,6 +365,7 @@ extern "C" int mpwsd_load_code(int n, const uint8_t *G, const uint8_t *frozen, i
         {(void **)&d.pat_tiles, tiles.data(), tiles.size() * 2},
         {(void **)&d.crc_masks, masks.data(), masks.size() * 8},
         {(void **)&d.gen_rows, gen.data(), gen.size() * 8},
+        {(void **)&d.osd_sets, osd_sets.data(), osd_sets.size() * 4},
     };
     for (auto &u : ups) {
         e = dev_alloc(u.dst, u.bytes);
@@ -527,6 +549,7 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
         oa.B = B;
         oa.L = L;
         oa.order = o.osd_order;
+        oa.ncand = osd_candidates(d.k, o.osd_order);
         oa.mode = 0;
         oa.rule = o.stage1_rule;
         oa.use_crc = d.crc_len > 0 && !o.always_on;
@@ -713,6 +736,8 @@ extern "C" int mpwsd_stage1_list(mpwsd_code *code, const float *y_dev, int64_t B
     return MPWSD_OK;
 }
 
+static_assert(MPWSD_MAX_OSD_ORDER == kOsdMaxOrder, "the OSD set table covers every allowed order");
+
 extern "C" int mpwsd_osd_list(mpwsd_code *code, const float *y_dev, int64_t B, int order, int L, uint64_t *list_cw_dev,
                               int64_t *list_d_dev, void *stream) {
     if (!code) return fail(MPWSD_EINVAL, "code is NULL");
@@ -727,6 +752,7 @@ extern "C" int mpwsd_osd_list(mpwsd_code *code, const float *y_dev, int64_t B, i
     oa.B = B;
     oa.L = L;
     oa.order = order;
+    oa.ncand = osd_candidates(code->d.k, order);
     oa.mode = 1;
     oa.list_cw = list_cw_dev;
     oa.list_d = list_d_dev;

@@ -14,13 +14,18 @@
 //      2 sum |y| + 4 D(c)): exact integers;
 //   7. the min(L, #candidates) smallest (D, number), ascending.
 // GPU mapping: one warp per frame. Element j of the frame sits in lane j % 32
-// (so a ballot over lanes gives 32 consecutive bits of a bit vector); the
-// generator rows sit one per lane (k <= 32) for the elimination; D of a
-// candidate is sum_b popc(e & plane_b) << b over the bit planes of |y|, no
-// data-dependent loops; the running list lives one entry per lane, and a
-// candidate that beats its last entry is inserted with a ballot and one
-// shuffle. The decode tail (CRC early exit, slots, trajectories) matches the
-// SC-list kernel's.
+// (so a ballot over lanes gives 32 consecutive bits of a bit vector). The
+// positions are ranked by a bitonic sort of (|g| << 8 | 255 - j) keys held in
+// registers. The generator rows sit one per lane (k <= 32) for the
+// elimination and are then moved so that lane t holds row t of G_sys. The
+// candidates come from a table of row sets in candidate-number order, 32 per
+// step, one per lane; a lane forms its error pattern from the rows by
+// shuffles, and D = sum over the bytes of the pattern of a per-frame byte
+// table (tab[b][v] = sum of |g_j| over the set bits of v, j = 8b + bit), so a
+// candidate costs n/8 lookups. The running list lives one entry per lane; a
+// candidate below its last entry is inserted with a ballot and one shuffle.
+// The decode tail (CRC early exit, slots, trajectories) matches the SC-list
+// kernel's.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -31,67 +36,66 @@ namespace {
 constexpr int kOsdWarps = 4;
 constexpr unsigned kAll = 0xffffffffu;
 
-__device__ __forceinline__ uint32_t binom(int n, int r) {  // C(n, r) for 0 <= r <= 4
-    if (n < r || n < 0) return 0;
-    switch (r) {
-        case 0: return 1;
-        case 1: return (uint32_t)n;
-        case 2: return (uint32_t)(n * (n - 1) / 2);
-        case 3: return (uint32_t)(n * (n - 1) * (n - 2) / 6);
-        default: return (uint32_t)((n * (n - 1) * (n - 2) / 6) * (n - 3) / 4);
-    }
-}
-
-// number of a candidate: sets of fewer rows first, then the lexicographic rank
-// of the sorted set (c[0] < ... < c[w-1]) among the w-subsets of k rows
-__device__ __forceinline__ uint32_t cand_number(int k, int w, const int (&c)[4]) {
-    uint32_t base = 0;
-    for (int v = 0; v < w; ++v) base += binom(k, v);
-    uint32_t r = binom(k, w) - 1;
-    for (int t = 0; t < w; ++t) r -= binom(k - 1 - c[t], w - t);
-    return base + r;
-}
-
-// inverse of cand_number
-__device__ __forceinline__ int cand_set(int k, uint32_t idx, int (&c)[4]) {
-    int w = 0;
-    while (w < 4 && idx >= binom(k, w)) idx -= binom(k, w++);
-    int start = 0;
-    for (int t = 0; t < w; ++t) {
-        for (int v = start; v < k; ++v) {
-            const uint32_t rest = binom(k - v - 1, w - t - 1);
-            if (idx < rest) {
-                c[t] = v;
-                start = v + 1;
-                break;
-            }
-            idx -= rest;
-        }
-    }
-    return w;
-}
-
 template <int N>
-struct OsdSmem {
-    static constexpr int W = (N + 63) / 64;
-    int g[kOsdWarps][N];              // round(y 2^19)
-    uint32_t key[kOsdWarps][N];       // |g| << 8 | (255 - j): larger = more reliable
-    uint8_t perm[kOsdWarps][N];       // positions by decreasing reliability
-    uint8_t mrb[kOsdWarps][32];       // basis position of pivot t
-    uint64_t gs[kOsdWarps][32][W];    // G_sys rows by pivot order
-    uint64_t plane[kOsdWarps][24][W]; // bit planes of |g|
+struct OsdWarpSmem {
+    static constexpr int NB = N / 8;
+    uint32_t tab[NB][256];  // tab[b][v] = sum of |g_j| over the set bits i of v, j = 8b + i
+    int g[N];               // round(y 2^19)
+    uint8_t perm[N];        // positions by decreasing reliability
+    uint8_t mrb[32];        // basis position of pivot t
+    uint8_t lane_of[32];    // lane that holds the row of pivot t after the elimination
 };
 
+// bitonic sort of the warp's N keys (element e of lane l is entry 32 e + l),
+// descending; keys are distinct
 template <int N>
-__device__ __forceinline__ uint32_t discrepancy(const uint64_t (&e)[(N + 63) / 64], const uint64_t (*plane)[(N + 63) / 64],
-                                                int nb) {
-    constexpr int W = (N + 63) / 64;
-    uint32_t d = 0;
-    for (int b = 0; b < nb; ++b) {
-        int cnt = 0;
+__device__ __forceinline__ void sort_desc(uint32_t (&key)[N / 32], int lane) {
+    constexpr int EPL = N / 32;
 #pragma unroll
-        for (int w = 0; w < W; ++w) cnt += __popcll(e[w] & plane[b][w]);
-        d += (uint32_t)cnt << b;
+    for (int s = 2; s <= N; s <<= 1) {
+#pragma unroll
+        for (int d = s >> 1; d > 0; d >>= 1) {
+            if (d >= 32) {
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) {
+                    const int ep = e ^ (d >> 5);
+                    if (ep > e) {
+                        // entry 32 e + lane is the lower one of the pair
+                        const bool desc = ((32 * e + lane) & s) == 0;
+                        const uint32_t mx = max(key[e], key[ep]), mn = min(key[e], key[ep]);
+                        key[e] = desc ? mx : mn;
+                        key[ep] = desc ? mn : mx;
+                    }
+                }
+            } else {
+                const bool lower = (lane & d) == 0;
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) {
+                    const uint32_t o = __shfl_xor_sync(kAll, key[e], d);
+                    const bool desc = ((32 * e + lane) & s) == 0;
+                    key[e] = (lower == desc) ? max(key[e], o) : min(key[e], o);
+                }
+            }
+        }
+    }
+}
+
+// bit p of a W-word vector, without a dynamically indexed (local-memory) array
+template <int W>
+__device__ __forceinline__ bool bit_at(const uint64_t (&v)[W], int p) {
+    uint64_t x = v[0];
+#pragma unroll
+    for (int w = 1; w < W; ++w) x = (p >> 6) == w ? v[w] : x;
+    return (x >> (p & 63)) & 1ull;
+}
+
+template <int N>
+__device__ __forceinline__ uint32_t discrepancy(const uint64_t (&e)[(N + 63) / 64], const uint32_t (*tab)[256]) {
+    uint32_t d = 0;
+#pragma unroll
+    for (int b = 0; b < N / 8; ++b) {
+        const uint32_t h = (uint32_t)(e[b >> 3] >> (32 * ((b >> 2) & 1)));
+        d += tab[b][__byte_perm(h, 0u, 0x4440u | (uint32_t)(b & 3))];
     }
     return d;
 }
@@ -100,52 +104,53 @@ template <int N>
 __global__ void __launch_bounds__(kOsdWarps * 32) osd_kernel(const OsdArgs a, const CodeDev c) {
     constexpr int W = (N + 63) / 64;
     constexpr int EPL = N / 32;  // elements per lane: element j = lane + 32 e
-    __shared__ OsdSmem<N> sm;
+    extern __shared__ __align__(16) unsigned char osd_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    OsdWarpSmem<N> &sm = reinterpret_cast<OsdWarpSmem<N> *>(osd_smem)[warp];
     const int k = c.k;
     const int L = a.L;
+    // lane bit masks for the byte tables: entry 8 lane + u has bits 3..7 = lane
+    uint32_t lm[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) lm[i] = 0u - (((uint32_t)lane >> i) & 1u);
     for (int64_t f = (int64_t)blockIdx.x * kOsdWarps + warp; f < a.B; f += (int64_t)gridDim.x * kOsdWarps) {
-        // ---- 1. hard decisions, reliabilities, bit planes ----
-        int g[EPL];
+        // ---- 1. hard decisions, reliabilities ----
+        uint32_t key[EPL];
         uint32_t hdh[EPL];  // 32-bit halves of hd: half e holds elements 32e .. 32e+31
         int asum = 0;
-        uint32_t amax = 0;
 #pragma unroll
         for (int e = 0; e < EPL; ++e) {
             const int j = lane + 32 * e;
-            g[e] = grid_q(a.y[f * N + j]);
-            const uint32_t ag = (uint32_t)abs(g[e]);
+            const int g = grid_q(a.y[f * N + j]);
+            const uint32_t ag = (uint32_t)abs(g);
             asum += (int)ag;
-            amax = max(amax, ag);
-            sm.g[warp][j] = g[e];
-            sm.key[warp][j] = (ag << 8) | (uint32_t)(255 - j);
-            hdh[e] = __ballot_sync(kAll, g[e] < 0);
+            sm.g[j] = g;
+            key[e] = (ag << 8) | (uint32_t)(255 - j);
+            hdh[e] = __ballot_sync(kAll, g < 0);
         }
         asum = __reduce_add_sync(kAll, asum);  // sum_j |g_j| < 2^30
-        amax = __reduce_max_sync(kAll, amax);
-        const int nb = 32 - __clz((int)amax);
-        for (int b = 0; b < nb; ++b) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const uint32_t lo = __ballot_sync(kAll, ((uint32_t)abs(g[(2 * w) % EPL]) >> b) & 1u);
-                const uint32_t hi = (2 * w + 1 < EPL) ? __ballot_sync(kAll, ((uint32_t)abs(g[(2 * w + 1) % EPL]) >> b) & 1u) : 0u;
-                if (lane == 0) sm.plane[warp][b][w] = (uint64_t)lo | ((uint64_t)hi << 32);
-            }
-        }
         uint64_t hdw[W];
 #pragma unroll
         for (int w = 0; w < W; ++w)
             hdw[w] = (uint64_t)hdh[(2 * w) % EPL] | ((2 * w + 1 < EPL) ? (uint64_t)hdh[(2 * w + 1) % EPL] << 32 : 0ull);
         __syncwarp();
-        // ---- 2. positions by decreasing reliability (rank by counting; keys are distinct) ----
-#pragma unroll
-        for (int e = 0; e < EPL; ++e) {
-            const int j = lane + 32 * e;
-            const uint32_t kj = sm.key[warp][j];
-            int r = 0;
-            for (int i = 0; i < N; ++i) r += sm.key[warp][i] > kj;
-            sm.perm[warp][r] = (uint8_t)j;
+        // ---- byte tables of |g| ----
+#pragma unroll 2
+        for (int b = 0; b < N / 8; ++b) {
+            const int4 q0 = *reinterpret_cast<const int4 *>(&sm.g[8 * b]);
+            const int4 q1 = *reinterpret_cast<const int4 *>(&sm.g[8 * b + 4]);
+            const uint32_t a0 = abs(q0.x), a1 = abs(q0.y), a2 = abs(q0.z);
+            const uint32_t hi = (abs(q0.w) & lm[0]) + (abs(q1.x) & lm[1]) + (abs(q1.y) & lm[2]) + (abs(q1.z) & lm[3]) +
+                                (abs(q1.w) & lm[4]);
+            const uint32_t s01 = a0 + a1, s02 = a0 + a2, s12 = a1 + a2;
+            uint4 *dst = reinterpret_cast<uint4 *>(&sm.tab[b][8 * lane]);
+            dst[0] = make_uint4(hi, hi + a0, hi + a1, hi + s01);
+            dst[1] = make_uint4(hi + a2, hi + s02, hi + s12, hi + s01 + a2);
         }
+        // ---- 2. positions by decreasing reliability ----
+        sort_desc<N>(key, lane);
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) sm.perm[32 * e + lane] = (uint8_t)(255 - (key[e] & 255u));
         __syncwarp();
         // ---- 3. Gauss-Jordan with pivots in reliability order ----
         uint64_t row[W];
@@ -154,8 +159,8 @@ __global__ void __launch_bounds__(kOsdWarps * 32) osd_kernel(const OsdArgs a, co
         bool used = lane >= k;
         int piv = 0, found = 0;
         for (int q = 0; q < N && found < k; ++q) {
-            const int p = sm.perm[warp][q];
-            const bool bit = lane < k && ((row[p >> 6] >> (p & 63)) & 1ull);
+            const int p = sm.perm[q];
+            const bool bit = lane < k && bit_at<W>(row, p);
             const unsigned m = __ballot_sync(kAll, bit && !used);
             if (!m) continue;  // column dependent on the chosen ones
             const int r = __ffs(m) - 1;
@@ -168,28 +173,34 @@ __global__ void __launch_bounds__(kOsdWarps * 32) osd_kernel(const OsdArgs a, co
                 used = true;
                 piv = found;
             }
-            if (lane == 0) sm.mrb[warp][found] = (uint8_t)p;
+            if (lane == 0) sm.mrb[found] = (uint8_t)p;
             ++found;
         }
+        if (lane < k) sm.lane_of[piv] = (uint8_t)lane;
         __syncwarp();
-        // ---- 4. G_sys by pivot order, c0, e0 = c0 xor hd ----
+        // ---- 4. lane t takes row t of G_sys; c0; e0 = c0 xor hd ----
+        uint64_t rowp[W];
         bool take = false;
-        if (lane < k) {
+        {
+            const int src = lane < k ? sm.lane_of[lane] : 0;
 #pragma unroll
-            for (int w = 0; w < W; ++w) sm.gs[warp][piv][w] = row[w];
-            const int p = sm.mrb[warp][piv];
-            take = (hdw[p >> 6] >> (p & 63)) & 1ull;
+            for (int w = 0; w < W; ++w) rowp[w] = __shfl_sync(kAll, row[w], src);
+            if (lane < k) {
+                const int p = sm.mrb[lane];
+                take = bit_at<W>(hdw, p);
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; ++w) rowp[w] = 0ull;
+            }
         }
         uint64_t e0[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            const uint64_t x = take ? row[w] : 0ull;
+            const uint64_t x = take ? rowp[w] : 0ull;
             const uint32_t lo = __reduce_xor_sync(kAll, (uint32_t)x), hi = __reduce_xor_sync(kAll, (uint32_t)(x >> 32));
             e0[w] = (((uint64_t)hi << 32) | lo) ^ hdw[w];
         }
-        __syncwarp();
         // ---- 5-7. candidates, their discrepancy, the running list (one entry per lane) ----
-        const uint64_t (*plane)[W] = sm.plane[warp];
         unsigned long long lkey = ~0ull;  // list entry `lane` (D << 32 | number), ascending
         auto offer = [&](bool valid, unsigned long long key) {
             unsigned long long thr = __shfl_sync(kAll, lkey, L - 1);
@@ -206,60 +217,39 @@ __global__ void __launch_bounds__(kOsdWarps * 32) osd_kernel(const OsdArgs a, co
                 thr = __shfl_sync(kAll, lkey, L - 1);
             }
         };
-        auto score = [&](int w, const int (&cs)[4]) {
+        // e ^= rows of the set packed in st (5 bits per row, the size in bits 20..22)
+        auto flip_rows = [&](uint64_t (&e)[W], uint32_t st) {
+            const int w = (int)(st >> 20);
+            const int wmax = (int)__reduce_max_sync(kAll, (unsigned)w);
+            for (int t = 0; t < wmax; ++t) {
+                const int src = (int)(st >> (5 * t)) & 31;
+#pragma unroll
+                for (int x = 0; x < W; ++x) {
+                    const uint64_t r = __shfl_sync(kAll, rowp[x], src);
+                    if (t < w) e[x] ^= r;
+                }
+            }
+        };
+        const uint32_t(*tab)[256] = sm.tab;
+        for (int base = 0; base < a.ncand; base += 32) {
+            const int idx = base + lane;
+            const bool valid = idx < a.ncand;
+            const uint32_t st = valid ? __ldg(c.osd_sets + idx) : 0u;
             uint64_t e[W];
 #pragma unroll
             for (int x = 0; x < W; ++x) e[x] = e0[x];
-            for (int t = 0; t < w; ++t)
-#pragma unroll
-                for (int x = 0; x < W; ++x) e[x] ^= sm.gs[warp][cs[t]][x];
-            const uint32_t d = discrepancy<N>(e, plane, nb);
-            return ((unsigned long long)d << 32) | cand_number(k, w, cs);
-        };
-        {
-            int cs[4] = {0, 0, 0, 0};
-            offer(lane == 0, score(0, cs));
+            flip_rows(e, st);
+            const uint32_t d = discrepancy<N>(e, tab);
+            offer(valid, ((unsigned long long)d << 32) | (unsigned)idx);
         }
-        if (a.order >= 1) {
-            int cs[4] = {lane, 0, 0, 0};
-            offer(lane < k, lane < k ? score(1, cs) : ~0ull);
-        }
-        if (a.order >= 2)
-            for (int i = 0; i + 1 < k; ++i) {
-                const int l = i + 1 + lane;
-                int cs[4] = {i, l, 0, 0};
-                offer(l < k, l < k ? score(2, cs) : ~0ull);
-            }
-        if (a.order >= 3)
-            for (int i = 0; i + 2 < k; ++i)
-                for (int i2 = i + 1; i2 + 1 < k; ++i2)
-                    for (int l = i2 + 1 + lane; l - lane < k; l += 32) {
-                        int cs[4] = {i, i2, l, 0};
-                        offer(l < k, l < k ? score(3, cs) : ~0ull);
-                    }
-        if (a.order >= 4)
-            for (int i = 0; i + 3 < k; ++i)
-                for (int i2 = i + 1; i2 + 2 < k; ++i2)
-                    for (int i3 = i2 + 1; i3 + 1 < k; ++i3) {
-                        const int l = i3 + 1 + lane;
-                        int cs[4] = {i, i2, i3, l};
-                        offer(l < k, l < k ? score(4, cs) : ~0ull);
-                    }
         // entry `lane` of the list: its codeword
         const int count = __popc(__ballot_sync(kAll, lkey != ~0ull));
         const bool valid = lane < count;
         uint64_t cw[W];
-        uint32_t dval = 0;
-        {
-            int cs[4] = {0, 0, 0, 0};
-            const int w = valid ? cand_set(k, (uint32_t)lkey, cs) : 0;
 #pragma unroll
-            for (int x = 0; x < W; ++x) cw[x] = e0[x] ^ hdw[x];
-            for (int t = 0; t < w; ++t)
-#pragma unroll
-                for (int x = 0; x < W; ++x) cw[x] ^= sm.gs[warp][cs[t]][x];
-            dval = (uint32_t)(lkey >> 32);
-        }
+        for (int x = 0; x < W; ++x) cw[x] = e0[x] ^ hdw[x];
+        flip_rows(cw, valid ? __ldg(c.osd_sets + (uint32_t)lkey) : 0u);
+        const uint32_t dval = (uint32_t)(lkey >> 32);
         if (a.mode == 1) {
             if (valid) {
 #pragma unroll
@@ -307,7 +297,7 @@ __global__ void __launch_bounds__(kOsdWarps * 32) osd_kernel(const OsdArgs a, co
                 uint32_t h2 = 0, l2 = 0;
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    const float v = (float)sm.g[warp][2 * w2 + e] * (1.0f / 524288.0f);
+                    const float v = (float)sm.g[2 * w2 + e] * (1.0f / 524288.0f);
                     const __nv_bfloat16 h = __float2bfloat16_rn(v);
                     const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
                     h2 |= (uint32_t)__bfloat16_as_ushort(h) << (16 * e);
@@ -340,16 +330,22 @@ __global__ void __launch_bounds__(kOsdWarps * 32) osd_kernel(const OsdArgs a, co
 
 template <int N>
 cudaError_t launch_n(const CodeDev &c, const OsdArgs &a, cudaStream_t s) {
+    constexpr int smem = kOsdWarps * (int)sizeof(OsdWarpSmem<N>);
+    static_assert(sizeof(OsdWarpSmem<N>) % 16 == 0, "per-warp slices stay 16-byte aligned");
+    cudaError_t e = cudaFuncSetAttribute(osd_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
     const int64_t blocks = std::min<int64_t>((a.B + kOsdWarps - 1) / kOsdWarps, (int64_t)c.num_sms * 16);
     if (blocks <= 0) return cudaSuccess;
-    osd_kernel<N><<<(unsigned)blocks, kOsdWarps * 32, 0, s>>>(a, c);
+    osd_kernel<N><<<(unsigned)blocks, kOsdWarps * 32, smem, s>>>(a, c);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_osd(const CodeDev &c, const OsdArgs &a, cudaStream_t s) {
-    if (c.k > 32 || a.L < 1 || a.L > 32 || a.order < 0 || a.order > 4) return cudaErrorInvalidValue;
+    if (c.k > 32 || !c.osd_sets || a.L < 1 || a.L > 32 || a.order < 0 || a.order > 4 ||
+        a.ncand != osd_candidates(c.k, a.order))
+        return cudaErrorInvalidValue;
     if (c.n == 32) return launch_n<32>(c, a, s);
     if (c.n == 64) return launch_n<64>(c, a, s);
     if (c.n == 128) return launch_n<128>(c, a, s);
