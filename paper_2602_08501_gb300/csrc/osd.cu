@@ -35,15 +35,30 @@ namespace {
 
 constexpr int kOsdWarps = 4;
 constexpr unsigned kAll = 0xffffffffu;
+constexpr int kMergeMin = 8;  // more entries than this in one step: sort and merge instead of inserting
+
+// The discrepancy tables cut each 64-position word of a pattern into chunks of
+// 6 bits (the last one narrower): table t of word x covers positions 64 x + 6 c
+// .. + width - 1, and entry v is the sum of |g| over the set bits of v. A table
+// has 64 entries (two per shared-memory bank), so the 32 lanes of a lookup
+// meet at most two-way bank conflicts, and a warp's tables take 5.5 KB (n =
+// 128), which leaves room for 32 warps per SM.
+template <int N>
+struct OsdGeom {
+    static constexpr int W = (N + 63) / 64;
+    static constexpr int BITS = N < 64 ? N : 64;  // positions per word
+    static constexpr int CPW = (BITS + 5) / 6;    // chunks per word
+    static constexpr int NT = W * CPW;            // tables
+};
 
 template <int N>
 struct OsdWarpSmem {
-    static constexpr int NB = N / 8;
-    uint32_t tab[NB][256];  // tab[b][v] = sum of |g_j| over the set bits i of v, j = 8b + i
-    int g[N];               // round(y 2^19)
-    uint8_t perm[N];        // positions by decreasing reliability
-    uint8_t mrb[32];        // basis position of pivot t
-    uint8_t lane_of[32];    // lane that holds the row of pivot t after the elimination
+    uint32_t tab[OsdGeom<N>::NT][64];  // first: 256-byte aligned (see osd_kernel)
+    uint32_t a[N];                     // |round(y 2^19)|
+    uint8_t perm[N];                   // positions by decreasing reliability
+    uint8_t mrb[32];                   // basis position of pivot t
+    uint8_t lane_of[32];               // lane that holds the row of pivot t after the elimination
+    uint8_t pad[(256 - (N * 5 + 64) % 256) % 256];
 };
 
 // bitonic sort of the warp's N keys (element e of lane l is entry 32 e + l),
@@ -89,27 +104,53 @@ __device__ __forceinline__ bool bit_at(const uint64_t (&v)[W], int p) {
     return (x >> (p & 63)) & 1ull;
 }
 
+// D of the pattern e: one lookup per chunk. tab_base is the shared-window
+// address of the warp's tables (256-byte aligned, so the entry offset ORs in).
 template <int N>
-__device__ __forceinline__ uint32_t discrepancy(const uint64_t (&e)[(N + 63) / 64], const uint32_t (*tab)[256]) {
-    uint32_t d = 0;
+__device__ __forceinline__ uint32_t discrepancy(const uint64_t (&e)[(N + 63) / 64], uint32_t tab_base) {
+    using Gm = OsdGeom<N>;
+    uint32_t d[4] = {0u, 0u, 0u, 0u};  // four partial sums: independent add chains
+    uint32_t pend = 0u;                 // values are added in pairs (three-input adds)
 #pragma unroll
-    for (int b = 0; b < N / 8; ++b) {
-        const uint32_t h = (uint32_t)(e[b >> 3] >> (32 * ((b >> 2) & 1)));
-        d += tab[b][__byte_perm(h, 0u, 0x4440u | (uint32_t)(b & 3))];
+    for (int x = 0; x < Gm::W; ++x) {
+        const uint32_t lo = (uint32_t)e[x], hi = (uint32_t)(e[x] >> 32);
+#pragma unroll
+        for (int cc = 0; cc < Gm::CPW; ++cc) {
+            const int s = 6 * cc;
+            const int wd = Gm::BITS - s < 6 ? Gm::BITS - s : 6;
+            const uint32_t mask4 = ((1u << wd) - 1u) << 2;  // entry v at byte offset 4 v
+            uint32_t sh;  // the chunk, shifted so that it starts at bit 2
+            if (s == 0) sh = lo << 2;
+            else if (s + wd <= 32) sh = lo >> (s - 2);
+            else if (s >= 34) sh = hi >> (s - 34);
+            else sh = __funnelshift_r(lo, hi, s - 2);
+            // table offset as a constant displacement of the load
+            const uint32_t addr = ((sh & mask4) | tab_base) + (uint32_t)((x * Gm::CPW + cc) * 256);
+            uint32_t v;
+            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+            const int t = x * Gm::CPW + cc;
+            if (t & 1) d[(t >> 1) & 3] += pend + v;
+            else pend = v;
+        }
     }
-    return d;
+    if (Gm::NT & 1) d[0] += pend;
+    return (d[0] + d[1]) + (d[2] + d[3]);
 }
 
 template <int N>
-__global__ void __launch_bounds__(kOsdWarps * 32) osd_kernel(const OsdArgs a, const CodeDev c) {
+__global__ void __launch_bounds__(kOsdWarps * 32, 8) osd_kernel(const OsdArgs a, const CodeDev c) {
     constexpr int W = (N + 63) / 64;
     constexpr int EPL = N / 32;  // elements per lane: element j = lane + 32 e
     extern __shared__ __align__(16) unsigned char osd_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    OsdWarpSmem<N> &sm = reinterpret_cast<OsdWarpSmem<N> *>(osd_smem)[warp];
+    // round the dynamic window up to 256 bytes (the launch adds the slack)
+    const uint32_t win = (uint32_t)__cvta_generic_to_shared(osd_smem);
+    const uint32_t win256 = (win + 255u) & ~255u;
+    OsdWarpSmem<N> &sm = reinterpret_cast<OsdWarpSmem<N> *>(osd_smem + (win256 - win))[warp];
+    const uint32_t tab_base = win256 + (uint32_t)(warp * sizeof(OsdWarpSmem<N>));
     const int k = c.k;
     const int L = a.L;
-    // lane bit masks for the byte tables: entry 8 lane + u has bits 3..7 = lane
+    // lane bit masks for the tables: entries 2 lane and 2 lane + 1 have bits 1..5 = lane
     uint32_t lm[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) lm[i] = 0u - (((uint32_t)lane >> i) & 1u);
@@ -124,7 +165,7 @@ __global__ void __launch_bounds__(kOsdWarps * 32) osd_kernel(const OsdArgs a, co
             const int g = grid_q(a.y[f * N + j]);
             const uint32_t ag = (uint32_t)abs(g);
             asum += (int)ag;
-            sm.g[j] = g;
+            sm.a[j] = ag;
             key[e] = (ag << 8) | (uint32_t)(255 - j);
             hdh[e] = __ballot_sync(kAll, g < 0);
         }
@@ -134,18 +175,21 @@ __global__ void __launch_bounds__(kOsdWarps * 32) osd_kernel(const OsdArgs a, co
         for (int w = 0; w < W; ++w)
             hdw[w] = (uint64_t)hdh[(2 * w) % EPL] | ((2 * w + 1 < EPL) ? (uint64_t)hdh[(2 * w + 1) % EPL] << 32 : 0ull);
         __syncwarp();
-        // ---- byte tables of |g| ----
-#pragma unroll 2
-        for (int b = 0; b < N / 8; ++b) {
-            const int4 q0 = *reinterpret_cast<const int4 *>(&sm.g[8 * b]);
-            const int4 q1 = *reinterpret_cast<const int4 *>(&sm.g[8 * b + 4]);
-            const uint32_t a0 = abs(q0.x), a1 = abs(q0.y), a2 = abs(q0.z);
-            const uint32_t hi = (abs(q0.w) & lm[0]) + (abs(q1.x) & lm[1]) + (abs(q1.y) & lm[2]) + (abs(q1.z) & lm[3]) +
-                                (abs(q1.w) & lm[4]);
-            const uint32_t s01 = a0 + a1, s02 = a0 + a2, s12 = a1 + a2;
-            uint4 *dst = reinterpret_cast<uint4 *>(&sm.tab[b][8 * lane]);
-            dst[0] = make_uint4(hi, hi + a0, hi + a1, hi + s01);
-            dst[1] = make_uint4(hi + a2, hi + s02, hi + s12, hi + s01 + a2);
+        // ---- tables of |g| over 6-position chunks ----
+        {
+            using Gm = OsdGeom<N>;
+#pragma unroll
+            for (int x = 0; x < Gm::W; ++x)
+#pragma unroll
+                for (int cc = 0; cc < Gm::CPW; ++cc) {
+                    const int p0 = 64 * x + 6 * cc;
+                    const int wd = Gm::BITS - 6 * cc < 6 ? Gm::BITS - 6 * cc : 6;
+                    uint32_t hi = 0;  // bits 1 .. wd-1 of the entry come from the lane number
+#pragma unroll
+                    for (int i = 1; i < wd; ++i) hi += sm.a[p0 + i] & lm[i - 1];
+                    const uint32_t a0 = sm.a[p0];
+                    *reinterpret_cast<uint2 *>(&sm.tab[x * Gm::CPW + cc][2 * lane]) = make_uint2(hi, hi + a0);
+                }
         }
         // ---- 2. positions by decreasing reliability ----
         sort_desc<N>(key, lane);
@@ -205,6 +249,26 @@ __global__ void __launch_bounds__(kOsdWarps * 32) osd_kernel(const OsdArgs a, co
         auto offer = [&](bool valid, unsigned long long key) {
             unsigned long long thr = __shfl_sync(kAll, lkey, L - 1);
             unsigned m = __ballot_sync(kAll, valid && key < thr);
+            if (__popc(m) > kMergeMin) {
+                // many entries at once: sort the step's keys, then keep the L smallest of
+                // the two sorted runs (a bitonic merge); equal to inserting them one by one
+                unsigned long long x = (m >> lane) & 1u ? key : ~0ull;
+#pragma unroll
+                for (int sz = 2; sz <= 32; sz <<= 1)
+#pragma unroll
+                    for (int d = sz >> 1; d > 0; d >>= 1) {
+                        const unsigned long long o = __shfl_xor_sync(kAll, x, d);
+                        x = (((lane & d) == 0) == ((lane & sz) == 0)) ? min(x, o) : max(x, o);
+                    }
+                unsigned long long z = min(lkey, __shfl_sync(kAll, x, 31 - lane));
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) {
+                    const unsigned long long o = __shfl_xor_sync(kAll, z, d);
+                    z = (lane & d) == 0 ? min(z, o) : max(z, o);
+                }
+                lkey = lane < L ? z : ~0ull;
+                return;
+            }
             while (m) {
                 const int s = __ffs(m) - 1;
                 m &= m - 1;
@@ -230,17 +294,19 @@ __global__ void __launch_bounds__(kOsdWarps * 32) osd_kernel(const OsdArgs a, co
                 }
             }
         };
-        const uint32_t(*tab)[256] = sm.tab;
-        for (int base = 0; base < a.ncand; base += 32) {
-            const int idx = base + lane;
-            const bool valid = idx < a.ncand;
-            const uint32_t st = valid ? __ldg(c.osd_sets + idx) : 0u;
-            uint64_t e[W];
+        // two steps of 32 candidates at a time: two independent chains of lookups
+        for (int base = 0; base < a.ncand; base += 64) {
+            const int i0 = base + lane, i1 = base + 32 + lane;
+            const bool v0 = i0 < a.ncand, v1 = i1 < a.ncand;
+            const uint32_t s0 = v0 ? __ldg(c.osd_sets + i0) : 0u, s1 = v1 ? __ldg(c.osd_sets + i1) : 0u;
+            uint64_t e[W], f2[W];
 #pragma unroll
-            for (int x = 0; x < W; ++x) e[x] = e0[x];
-            flip_rows(e, st);
-            const uint32_t d = discrepancy<N>(e, tab);
-            offer(valid, ((unsigned long long)d << 32) | (unsigned)idx);
+            for (int x = 0; x < W; ++x) e[x] = f2[x] = e0[x];
+            flip_rows(e, s0);
+            flip_rows(f2, s1);
+            const uint32_t d0 = discrepancy<N>(e, tab_base), d1 = discrepancy<N>(f2, tab_base);
+            offer(v0, ((unsigned long long)d0 << 32) | (unsigned)i0);
+            if (__any_sync(kAll, v1)) offer(v1, ((unsigned long long)d1 << 32) | (unsigned)i1);
         }
         // entry `lane` of the list: its codeword
         const int count = __popc(__ballot_sync(kAll, lkey != ~0ull));
@@ -297,7 +363,8 @@ __global__ void __launch_bounds__(kOsdWarps * 32) osd_kernel(const OsdArgs a, co
                 uint32_t h2 = 0, l2 = 0;
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    const float v = (float)sm.g[2 * w2 + e] * (1.0f / 524288.0f);
+                    const int j = 2 * w2 + e;
+                    const float v = (bit_at<W>(hdw, j) ? -(float)sm.a[j] : (float)sm.a[j]) * (1.0f / 524288.0f);
                     const __nv_bfloat16 h = __float2bfloat16_rn(v);
                     const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
                     h2 |= (uint32_t)__bfloat16_as_ushort(h) << (16 * e);
@@ -330,8 +397,8 @@ __global__ void __launch_bounds__(kOsdWarps * 32) osd_kernel(const OsdArgs a, co
 
 template <int N>
 cudaError_t launch_n(const CodeDev &c, const OsdArgs &a, cudaStream_t s) {
-    constexpr int smem = kOsdWarps * (int)sizeof(OsdWarpSmem<N>);
-    static_assert(sizeof(OsdWarpSmem<N>) % 16 == 0, "per-warp slices stay 16-byte aligned");
+    constexpr int smem = kOsdWarps * (int)sizeof(OsdWarpSmem<N>) + 256;  // + slack for the 256-byte alignment
+    static_assert(sizeof(OsdWarpSmem<N>) % 256 == 0, "per-warp tables stay 256-byte aligned");
     cudaError_t e = cudaFuncSetAttribute(osd_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = std::min<int64_t>((a.B + kOsdWarps - 1) / kOsdWarps, (int64_t)c.num_sms * 16);
