@@ -179,6 +179,32 @@ MPWSD_API int mpwsd_decode(mpwsd_code *code, const float *y_dev, int64_t B, int 
                  uint64_t *cw_dev, uint16_t *flags_dev, void *stream);
 
 /*
+ * mpwsd_decode_host -- mpwsd_decode on HOST buffers: the copies to and from the
+ * device are part of the call and overlap the decode. The paper has no
+ * counterpart: this is an interface of the library.
+ *
+ *   y_host     host, B x n FP32, row-major; page-locked (cudaHostAlloc /
+ *              cudaHostRegister) for the copies to overlap, and required to be
+ *              page-locked when opts->use_graph is set.
+ *   cw_host    host, B x W uint64: decoded codewords.
+ *   flags_host host, B uint16: MPWSD_FLAG_* bits per frame.
+ *   B, L, T, opts, stream as in mpwsd_decode.
+ *
+ * The batch is cut into up to 8 chunks of at least 65,536 frames. Chunk i is
+ * copied to the device on a second stream of the handle while stage 1 runs on
+ * chunk i - 1 (stage 1 of a chunk waits for its copy); stage 2 then runs on
+ * the whole batch, and the results are copied back on `stream`. Everything is
+ * enqueued and the call returns without waiting: the host buffers must stay
+ * valid, and the results are there once `stream` has been synchronised. Uses
+ * the handle's internal workspace and device staging buffers for y, cw and
+ * flags (grown on demand with cudaMalloc; a growth waits for the device);
+ * concurrent calls on one handle must be serialised by the caller. Errors as
+ * in mpwsd_decode.
+ */
+MPWSD_API int mpwsd_decode_host(mpwsd_code *code, const float *y_host, int64_t B, int L, int T,
+                                const mpwsd_opts *opts, uint64_t *cw_host, uint16_t *flags_host, void *stream);
+
+/*
  * mpwsd_workspace_create -- device scratch for decodes of up to max_B frames
  * with lists of up to max_L. One workspace may be used by one stream at a
  * time; several workspaces let several streams decode concurrently with one

@@ -98,8 +98,9 @@ struct CodeDev {
 };
 
 struct SclArgs {
-    const float *y;
+    const float *y;      // frame f of this launch at y + f n; cw_out, flags_out indexed the same way
     int64_t B;
+    int64_t f0;          // decode: index of this launch's frame 0 in the whole batch (slot_frame)
     int L;
     int write_yhl;       // decode: also store each failing frame's y as bf16 hi / lo (tensor-core scoring)
     int mode;            // 0 = decode (CRC + compaction), 1 = list output
@@ -115,8 +116,9 @@ struct SclArgs {
 };
 
 struct OsdArgs {
-    const float *y;
+    const float *y;      // as in SclArgs
     int64_t B;
+    int64_t f0;
     int L;
     int order;
     int ncand;           // osd_candidates(k, order)

@@ -71,6 +71,12 @@ struct mpwsd_workspace {
     Workspace w;
 };
 
+// mpwsd_decode_host splits a batch into at most this many chunks, of at least
+// kHostChunkFrames frames each, so that the copy of chunk i + 1 overlaps
+// stage 1 of chunk i.
+constexpr int kHostChunks = 8;
+constexpr int64_t kHostChunkFrames = 65536;
+
 struct mpwsd_code {
     CodeDev d;
     std::vector<int> info;  // non-frozen indices, ascending
@@ -91,10 +97,11 @@ struct mpwsd_code {
         const void *ws, *y, *cw, *fl;
         int64_t ws_B, B;  // workspace layout (base, max_B, max_L) and the call
         int ws_L, L, T, mode, rule, aom, stage1, osd_order;
+        const void *hy, *hcw, *hfl;  // host buffers of mpwsd_decode_host (else NULL)
         bool operator==(const GraphKey &o) const {
             return ws == o.ws && ws_B == o.ws_B && ws_L == o.ws_L && y == o.y && cw == o.cw && fl == o.fl &&
                    B == o.B && L == o.L && T == o.T && mode == o.mode && rule == o.rule && aom == o.aom &&
-                   stage1 == o.stage1 && osd_order == o.osd_order;
+                   stage1 == o.stage1 && osd_order == o.osd_order && hy == o.hy && hcw == o.hcw && hfl == o.hfl;
         }
     };
     struct GraphEnt {
@@ -104,6 +111,14 @@ struct mpwsd_code {
     };
     std::vector<GraphEnt> graphs;
     cudaStream_t capture_stream = nullptr;
+    // mpwsd_decode_host: device staging buffers, the stream that carries the
+    // input copies, and the events that order each chunk's stage 1 after its copy
+    float *stage_y = nullptr;
+    uint64_t *stage_cw = nullptr;
+    uint16_t *stage_fl = nullptr;
+    int64_t stage_B = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_ev[kHostChunks + 1] = {};
 };
 
 namespace {
@@ -498,6 +513,12 @@ extern "C" void mpwsd_free_code(mpwsd_code *code) {
     for (auto e : code->pool) cudaEventDestroy(e);
     for (auto &g : code->graphs) cudaGraphExecDestroy(g.exec);
     if (code->capture_stream) cudaStreamDestroy(code->capture_stream);
+    if (code->copy_stream) cudaStreamDestroy(code->copy_stream);
+    for (auto e : code->copy_ev)
+        if (e) cudaEventDestroy(e);
+    cudaFree(code->stage_y);
+    cudaFree(code->stage_cw);
+    cudaFree(code->stage_fl);
     mpwsd_workspace_free(code->default_ws);
     free_code_device(code->d);
     delete code;
@@ -538,15 +559,23 @@ static cudaError_t launch_score(mpwsd_code *code, int mode, const ScoreArgs &a, 
     return timed_launch(code, MPWSD_KERNEL_SCORE_TC, s, [&] { return launch_score_tc(code->d, a, s); });
 }
 
-static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int64_t B, int L, int T,
-                       const mpwsd_opts &o, uint64_t *cw_dev, uint16_t *flags_dev, cudaStream_t s) {
+// Host buffers of mpwsd_decode_host: y is copied in chunk by chunk on the copy
+// stream, and the results are copied back on the decode stream at the end.
+struct HostIO {
+    const float *y = nullptr;
+    uint64_t *cw = nullptr;
+    uint16_t *fl = nullptr;
+};
+
+static cudaError_t stage1_launch(mpwsd_code *code, Workspace &ws, const float *y_dev, int64_t f0, int64_t B, int L,
+                                 const mpwsd_opts &o, uint64_t *cw_dev, uint16_t *flags_dev, cudaStream_t s) {
     CodeDev &d = code->d;
-    cudaError_t e = cudaMemsetAsync(ws.counters, 0, 64 * sizeof(int), s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    const int W = d.W;
     if (o.stage1 == MPWSD_STAGE1_OSD) {
         OsdArgs oa{};
-        oa.y = y_dev;
+        oa.y = y_dev + f0 * d.n;
         oa.B = B;
+        oa.f0 = f0;
         oa.L = L;
         oa.order = o.osd_order;
         oa.ncand = osd_candidates(d.k, o.osd_order);
@@ -554,23 +583,49 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
         oa.rule = o.stage1_rule;
         oa.use_crc = d.crc_len > 0 && !o.always_on;
         oa.write_yhl = o.score_mode == MPWSD_SCORE_BF16X2;
-        oa.cw_out = cw_dev;
-        oa.flags_out = flags_dev;
+        oa.cw_out = cw_dev + f0 * W;
+        oa.flags_out = flags_dev + f0;
         oa.ws = ws;
-        e = timed_launch(code, MPWSD_KERNEL_OSD, s, [&] { return launch_osd(d, oa, s); });
+        return timed_launch(code, MPWSD_KERNEL_OSD, s, [&] { return launch_osd(d, oa, s); });
+    }
+    SclArgs sa{};
+    sa.y = y_dev + f0 * d.n;
+    sa.B = B;
+    sa.f0 = f0;
+    sa.L = L;
+    sa.mode = 0;
+    sa.rule = o.stage1_rule;
+    sa.use_crc = d.crc_len > 0 && !o.always_on;
+    sa.cw_out = cw_dev + f0 * W;
+    sa.flags_out = flags_dev + f0;
+    sa.ws = ws;
+    sa.write_yhl = o.score_mode == MPWSD_SCORE_BF16X2;
+    return timed_launch(code, MPWSD_KERNEL_SCL, s, [&] { return launch_scl(d, sa, s); });
+}
+
+static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int64_t B, int L, int T,
+                       const mpwsd_opts &o, uint64_t *cw_dev, uint16_t *flags_dev, cudaStream_t s,
+                       const HostIO *host = nullptr) {
+    CodeDev &d = code->d;
+    cudaError_t e = cudaMemsetAsync(ws.counters, 0, 64 * sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if (!host) {
+        e = stage1_launch(code, ws, y_dev, 0, B, L, o, cw_dev, flags_dev, s);
     } else {
-        SclArgs sa{};
-        sa.y = y_dev;
-        sa.B = B;
-        sa.L = L;
-        sa.mode = 0;
-        sa.rule = o.stage1_rule;
-        sa.use_crc = d.crc_len > 0 && !o.always_on;
-        sa.cw_out = cw_dev;
-        sa.flags_out = flags_dev;
-        sa.ws = ws;
-        sa.write_yhl = o.score_mode == MPWSD_SCORE_BF16X2;
-        e = timed_launch(code, MPWSD_KERNEL_SCL, s, [&] { return launch_scl(d, sa, s); });
+        // chunk i is copied on the copy stream, then its stage 1 runs on s; the
+        // copies start after everything already on s (which may still read y_dev)
+        const int nch = (int)std::max<int64_t>(1, std::min<int64_t>(kHostChunks, B / kHostChunkFrames));
+        cudaEvent_t fork = code->copy_ev[kHostChunks];
+        e = cudaEventRecord(fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(code->copy_stream, fork, 0);
+        for (int i = 0; i < nch && e == cudaSuccess; ++i) {
+            const int64_t a = B * i / nch, b = B * (i + 1) / nch;
+            e = cudaMemcpyAsync((void *)(y_dev + a * d.n), host->y + a * d.n, (size_t)(b - a) * d.n * sizeof(float),
+                                cudaMemcpyHostToDevice, code->copy_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(code->copy_ev[i], code->copy_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, code->copy_ev[i], 0);
+            if (e == cudaSuccess) e = stage1_launch(code, ws, y_dev, a, b - a, L, o, cw_dev, flags_dev, s);
+        }
     }
     if (e != cudaSuccess) return cuda_fail(e, "stage-1 launch");
     for (int it = 0; it < T; ++it) {
@@ -598,6 +653,12 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
     }
     e = timed_launch(code, MPWSD_KERNEL_FINAL, s, [&] { return launch_final(d, ws, L, T, B, cw_dev, flags_dev, s); });
     if (e != cudaSuccess) return cuda_fail(e, "final launch");
+    if (host) {
+        e = cudaMemcpyAsync(host->cw, cw_dev, (size_t)B * d.W * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host->fl, flags_dev, (size_t)B * sizeof(uint16_t), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copying the results to the host");
+    }
     return MPWSD_OK;
 }
 
@@ -605,10 +666,12 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
 // sequence is captured on the handle's private stream (nothing runs) and
 // instantiated; every call then launches the graph on the caller's stream.
 static int decode_graph(mpwsd_code *code, Workspace &ws, const float *y_dev, int64_t B, int L, int T,
-                        const mpwsd_opts &o, uint64_t *cw_dev, uint16_t *flags_dev, cudaStream_t s) {
+                        const mpwsd_opts &o, uint64_t *cw_dev, uint16_t *flags_dev, cudaStream_t s,
+                        const HostIO *host) {
     mpwsd_code::GraphKey key{ws.base,  y_dev, cw_dev, flags_dev,     ws.max_B,      B,
                              ws.max_L, L,     T,      o.score_mode, o.stage1_rule, o.always_on,
-                             o.stage1, o.osd_order};
+                             o.stage1, o.osd_order, host ? (const void *)host->y : nullptr,
+                             host ? (const void *)host->cw : nullptr, host ? (const void *)host->fl : nullptr};
     std::lock_guard<std::mutex> lk(code->mu);
     for (auto &g : code->graphs)
         if (g.key == key) {
@@ -623,7 +686,7 @@ static int decode_graph(mpwsd_code *code, Workspace &ws, const float *y_dev, int
     e = cudaStreamBeginCapture(code->capture_stream, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     t_capturing = true;
-    int st = decode_impl(code, ws, y_dev, B, L, T, o, cw_dev, flags_dev, code->capture_stream);
+    int st = decode_impl(code, ws, y_dev, B, L, T, o, cw_dev, flags_dev, code->capture_stream, host);
     t_capturing = false;
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(code->capture_stream, &graph);
@@ -634,6 +697,13 @@ static int decode_graph(mpwsd_code *code, Workspace &ws, const float *y_dev, int
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     size_t nodes = 0;
     cudaGraphGetNodes(graph, nullptr, &nodes);
+    std::vector<cudaGraphNode_t> list(nodes);
+    if (nodes) cudaGraphGetNodes(graph, list.data(), &nodes);
+    int kernels = 0;
+    for (auto nd : list) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+    }
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -642,7 +712,6 @@ static int decode_graph(mpwsd_code *code, Workspace &ws, const float *y_dev, int
         cudaGraphExecDestroy(code->graphs.front().exec);
         code->graphs.erase(code->graphs.begin());
     }
-    const int kernels = (int)nodes - 1;  // every node but the counter reset is a kernel
     code->graphs.push_back({key, exec, kernels});
     e = cudaGraphLaunch(exec, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
@@ -651,9 +720,10 @@ static int decode_graph(mpwsd_code *code, Workspace &ws, const float *y_dev, int
 }
 
 static int run_decode(mpwsd_code *code, Workspace &ws, const float *y_dev, int64_t B, int L, int T,
-                      const mpwsd_opts &o, uint64_t *cw_dev, uint16_t *flags_dev, cudaStream_t s) {
-    if (o.use_graph && !code->profiling) return decode_graph(code, ws, y_dev, B, L, T, o, cw_dev, flags_dev, s);
-    return decode_impl(code, ws, y_dev, B, L, T, o, cw_dev, flags_dev, s);
+                      const mpwsd_opts &o, uint64_t *cw_dev, uint16_t *flags_dev, cudaStream_t s,
+                      const HostIO *host = nullptr) {
+    if (o.use_graph && !code->profiling) return decode_graph(code, ws, y_dev, B, L, T, o, cw_dev, flags_dev, s, host);
+    return decode_impl(code, ws, y_dev, B, L, T, o, cw_dev, flags_dev, s, host);
 }
 
 static int check_decode_args(mpwsd_code *code, const float *y_dev, int64_t B, int L, int T, const mpwsd_opts *opts,
@@ -686,6 +756,30 @@ extern "C" int mpwsd_decode_ws(mpwsd_code *code, mpwsd_workspace *ws, const floa
     return run_decode(code, ws->w, y_dev, B, L, T, o, cw_dev, flags_dev, (cudaStream_t)stream);
 }
 
+// The handle's own workspace, grown to (B, L) if needed. Caller holds code->mu.
+static int default_workspace(mpwsd_code *code, int64_t B, int L, mpwsd_workspace **out) {
+    mpwsd_workspace *ws = code->default_ws;
+    if (!ws || ws->w.max_B < B || ws->w.max_L < L) {
+        const int64_t nb = std::max<int64_t>(B, ws ? ws->w.max_B : 0);
+        const int nl = std::max(L, ws ? ws->w.max_L : 0);
+        mpwsd_workspace *nw = nullptr;
+        int st = mpwsd_workspace_create(code, nb, nl, &nw);
+        if (st) return st;
+        // graphs recorded on the old workspace go with it
+        for (auto it = code->graphs.begin(); it != code->graphs.end();)
+            if (ws && it->key.ws == ws->w.base) {
+                cudaGraphExecDestroy(it->exec);
+                it = code->graphs.erase(it);
+            } else {
+                ++it;
+            }
+        mpwsd_workspace_free(ws);
+        code->default_ws = ws = nw;
+    }
+    *out = ws;
+    return MPWSD_OK;
+}
+
 extern "C" int mpwsd_decode(mpwsd_code *code, const float *y_dev, int64_t B, int L, int T, const mpwsd_opts *opts,
                             uint64_t *cw_dev, uint16_t *flags_dev, void *stream) {
     mpwsd_opts o;
@@ -695,26 +789,50 @@ extern "C" int mpwsd_decode(mpwsd_code *code, const float *y_dev, int64_t B, int
     mpwsd_workspace *ws;
     {
         std::lock_guard<std::mutex> lk(code->mu);
-        ws = code->default_ws;
-        if (!ws || ws->w.max_B < B || ws->w.max_L < L) {
-            const int64_t nb = std::max<int64_t>(B, ws ? ws->w.max_B : 0);
-            const int nl = std::max(L, ws ? ws->w.max_L : 0);
-            mpwsd_workspace *nw = nullptr;
-            st = mpwsd_workspace_create(code, nb, nl, &nw);
-            if (st) return st;
-            // graphs recorded on the old workspace go with it
-            for (auto it = code->graphs.begin(); it != code->graphs.end();)
-                if (ws && it->key.ws == ws->w.base) {
-                    cudaGraphExecDestroy(it->exec);
-                    it = code->graphs.erase(it);
-                } else {
-                    ++it;
-                }
-            mpwsd_workspace_free(ws);
-            code->default_ws = ws = nw;
-        }
+        st = default_workspace(code, B, L, &ws);
+        if (st) return st;
     }
     return run_decode(code, ws->w, y_dev, B, L, T, o, cw_dev, flags_dev, (cudaStream_t)stream);
+}
+
+extern "C" int mpwsd_decode_host(mpwsd_code *code, const float *y_host, int64_t B, int L, int T,
+                                 const mpwsd_opts *opts, uint64_t *cw_host, uint16_t *flags_host, void *stream) {
+    mpwsd_opts o;
+    int st = check_decode_args(code, y_host, B, L, T, opts, cw_host, flags_host, &o);
+    if (st) return st;
+    if (B == 0) return MPWSD_OK;
+    mpwsd_workspace *ws;
+    HostIO io;
+    io.y = y_host;
+    io.cw = cw_host;
+    io.fl = flags_host;
+    {
+        std::lock_guard<std::mutex> lk(code->mu);
+        st = default_workspace(code, B, L, &ws);
+        if (st) return st;
+        cudaError_t e = cudaSuccess;
+        if (!code->copy_stream) e = cudaStreamCreateWithFlags(&code->copy_stream, cudaStreamNonBlocking);
+        for (auto &ev : code->copy_ev)
+            if (e == cudaSuccess && !ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "creating the copy stream");
+        if (code->stage_B < B) {
+            // a growth waits for the device (cudaFree); graphs keyed on the old buffers never match again
+            cudaFree(code->stage_y);
+            cudaFree(code->stage_cw);
+            cudaFree(code->stage_fl);
+            code->stage_y = nullptr;
+            code->stage_cw = nullptr;
+            code->stage_fl = nullptr;
+            code->stage_B = 0;
+            e = dev_alloc((void **)&code->stage_y, (size_t)B * code->d.n * sizeof(float));
+            if (e == cudaSuccess) e = dev_alloc((void **)&code->stage_cw, (size_t)B * code->d.W * sizeof(uint64_t));
+            if (e == cudaSuccess) e = dev_alloc((void **)&code->stage_fl, (size_t)B * sizeof(uint16_t));
+            if (e != cudaSuccess) return cuda_fail(e, "allocating the staging buffers");
+            code->stage_B = B;
+        }
+    }
+    return run_decode(code, ws->w, code->stage_y, B, L, T, o, code->stage_cw, code->stage_fl, (cudaStream_t)stream,
+                      &io);
 }
 
 extern "C" int mpwsd_stage1_list(mpwsd_code *code, const float *y_dev, int64_t B, int L, uint64_t *list_cw_dev,

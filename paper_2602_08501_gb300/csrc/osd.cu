@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kOsdWarps * 32, 8) osd_kernel(const OsdArgs a,
         if (lane == 0) {
             slot = atomicAdd(&a.ws.counters[0], 1);
             base = atomicAdd(&a.ws.counters[1], count);
-            a.ws.slot_frame[slot] = (int)f;
+            a.ws.slot_frame[slot] = (int)(a.f0 + f);
             a.ws.slot_l1[slot] = (float)asum * (1.0f / 524288.0f);
         }
         slot = __shfl_sync(kAll, slot, 0);

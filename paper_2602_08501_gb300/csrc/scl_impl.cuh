@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32) scl_kernel(const
     if (sl == 0) {
         int l1 = 0;
         for (int j = 0; j < N; ++j) l1 += abs(cx.ych[j]);
-        a.ws.slot_frame[slot] = (int)frame;
+        a.ws.slot_frame[slot] = (int)(a.f0 + frame);
         a.ws.slot_l1[slot] = (float)l1 * (1.0f / 524288.0f);
     }
     if (a.write_yhl) {

@@ -79,6 +79,7 @@ def lib():
             "mpwsd_free_code": (None, [P]),
             "mpwsd_code_info": (i32, [P, P, P, P, P]),
             "mpwsd_decode": (i32, [P, P, i64, i32, i32, P, P, P, P]),
+            "mpwsd_decode_host": (i32, [P, P, i64, i32, i32, P, P, P, P]),
             "mpwsd_workspace_create": (i32, [P, i64, i32, ctypes.POINTER(P)]),
             "mpwsd_workspace_free": (None, [P]),
             "mpwsd_workspace_bytes": (i32, [P, i64, i32, ctypes.POINTER(ctypes.c_size_t)]),
@@ -125,6 +126,16 @@ def _dev(t, dtype, name):
 
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(t, dtype, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+        raise TypeError(f"{name} must be a host (CPU) tensor")
     if t.dtype != dtype or not t.is_contiguous():
         raise TypeError(f"{name} must be a contiguous {dtype} tensor")
     return ctypes.c_void_p(t.data_ptr())
@@ -241,6 +252,27 @@ class Code:
             _check(lib().mpwsd_decode(self._h, *args), "decode")
         else:
             _check(lib().mpwsd_decode_ws(self._h, workspace._h, *args), "decode_ws")
+        return cw_out, flags_out
+
+    def decode_host(self, y, L: int, T: int, score_mode="bf16x2", rule="top1", always_on=False, cw_out=None,
+                    flags_out=None, stream=None, use_graph: bool = False, osd_order: int | None = None):
+        """decode() on host (CPU) tensors: the library copies y in chunk by chunk,
+        overlapping the copies with stage 1, and copies the results back. Pinned
+        tensors let the copies overlap. Returns (cw, flags) host tensors, valid once
+        the stream has been synchronised."""
+        import torch
+
+        if y.dim() != 2 or y.shape[1] != self.n:
+            raise ValueError(f"y must be B x {self.n}")
+        B = int(y.shape[0])
+        if cw_out is None:
+            cw_out = torch.empty((B, self.W), dtype=torch.int64, pin_memory=y.is_pinned())
+        if flags_out is None:
+            flags_out = torch.empty((B,), dtype=torch.int16, pin_memory=y.is_pinned())
+        o = self._opts(score_mode, rule, always_on, use_graph, osd_order)
+        _check(lib().mpwsd_decode_host(self._h, _host(y, torch.float32, "y"), B, int(L), int(T), ctypes.byref(o),
+                                       _host(cw_out, torch.int64, "cw_out"), _host(flags_out, torch.int16, "flags_out"),
+                                       _stream_ptr(stream)), "decode_host")
         return cw_out, flags_out
 
     def stage1_list(self, y, L: int, stream=None):
