@@ -387,7 +387,7 @@ def run_ours(args, wl_cfg):
                     "frac": ach / (alu_peak / 1e12), "traffic": None, "kernel": "score_fp32",
                     "peak_kind": "152 SMs x 128 FP32 lanes x max SM clock"}
         if kname == "scl":
-            ops = frames * 4 * L * n * math.log2(n) / launches  # Table I: (4/3) L log2 N ED units x 3N
+            ops = frames * 4 * L * n * math.log2(n)  # per launch (one per step): Table I, (4/3) L log2 N ED units x 3N
             ach = ops / per_launch_s / 1e12
             src = src_hash("paper_2602_08501_gb300/csrc/scl_impl.cuh", "paper_2602_08501_gb300/csrc/internal.h")
             bpf = recorded_traffic("scl", src, "frame")
@@ -400,10 +400,14 @@ def run_ours(args, wl_cfg):
             kk = int(code.k)
             order = int(wl_cfg.get("osd", 0))
             ncand = sum(math.comb(kk, w) for w in range(order + 1))
-            ops = frames * n * (ncand + kk) / launches
+            ops = frames * n * (ncand + kk)  # per launch (one per step)
             ach = ops / per_launch_s / 1e12
+            src = src_hash("paper_2602_08501_gb300/csrc/osd.cu", "paper_2602_08501_gb300/csrc/common.cuh",
+                           "paper_2602_08501_gb300/csrc/internal.h")
+            bpf = recorded_traffic("osd", src, "frame")
+            tr = None if bpf is None else bpf * frames
             return {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "Top/s",
-                    "frac": ach / (alu_peak / 1e12), "traffic": None, "kernel": "osd",
+                    "frac": ach / (alu_peak / 1e12), "traffic": tr, "kernel": "osd",
                     "peak_kind": "152 SMs x 128 INT32 lanes x max SM clock", "ops_per_launch": ops}
         if kname == "hop":
             # bytes a row needs: its list entry (4 + 32), centre, D, state, 1/L of its frame's y row and
