@@ -25,7 +25,10 @@
 //               hi / lo, write the swizzled A tiles;
 //   warps 4-11  epilogue: warp 4 + 4h + q reads TMEM lane quadrant q (one row
 //               per thread) and column half h of every accumulator with
-//               tcgen05.ld x64, takes minima of 8-column groups with
+//               tcgen05.ld (x64 chunks for n = 64; for n = 128 x32 slices,
+//               the next one's load in flight while one is scanned, and the
+//               accumulator released once its last columns are in
+//               registers); takes minima of 8-column groups with
 //               three-input mins, and only groups that beat the row's
 //               admission threshold enter its running top-K; at the end of a
 //               unit the two halves of each row's list meet in shared memory.
@@ -171,7 +174,7 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 
 #define MPWSD_R8(i) "=r"(v[i + 0]), "=r"(v[i + 1]), "=r"(v[i + 2]), "=r"(v[i + 3]), "=r"(v[i + 4]), "=r"(v[i + 5]), \
                     "=r"(v[i + 6]), "=r"(v[i + 7])
-// 64 consecutive FP32 columns of this thread's TMEM lane
+// 64 consecutive FP32 columns of this thread's TMEM lane (load and wait)
 __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
@@ -184,6 +187,23 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// issue a load of 32 consecutive FP32 columns of this thread's TMEM lane (no wait)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : MPWSD_R8(0), MPWSD_R8(8), MPWSD_R8(16), MPWSD_R8(24)
+        : "r"(taddr));
+}
+#undef MPWSD_R8
+#define MPWSD_R8(i) "+r"(v[i + 0]), "+r"(v[i + 1]), "+r"(v[i + 2]), "+r"(v[i + 3]), "+r"(v[i + 4]), "+r"(v[i + 5]), \
+                    "+r"(v[i + 6]), "+r"(v[i + 7])
+// wait for this thread's outstanding TMEM loads; v (the last one's registers) is
+// passed through so that nothing reads it before the wait
+__device__ __forceinline__ void tmem_wait(uint32_t (&v)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : MPWSD_R8(0), MPWSD_R8(8), MPWSD_R8(16), MPWSD_R8(24)::"memory");
+}
 #undef MPWSD_R8
 
 __device__ __forceinline__ float fmin3(float a, float b, float c) {
@@ -193,8 +213,8 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
 }
 
 // minimum of the 8 values v[8g .. 8g+7]
-template <int G8>
-__device__ __forceinline__ float min8(const uint32_t (&v)[64]) {
+template <int G8, int CW>
+__device__ __forceinline__ float min8(const uint32_t (&v)[CW]) {
     return fmin3(fmin3(__uint_as_float(v[8 * G8]), __uint_as_float(v[8 * G8 + 1]), __uint_as_float(v[8 * G8 + 2])),
                  fmin3(__uint_as_float(v[8 * G8 + 3]), __uint_as_float(v[8 * G8 + 4]), __uint_as_float(v[8 * G8 + 5])),
                  fminf(__uint_as_float(v[8 * G8 + 6]), __uint_as_float(v[8 * G8 + 7])));
@@ -210,8 +230,8 @@ __device__ __forceinline__ float admit_thr(const float (&tv)[kTopK], float eps2)
 // Move every value of group G8 below the admission threshold into the running
 // list: take the group minimum, insert it (its lowest position on ties), blank
 // it, repeat. Usually zero or one round.
-template <int G8>
-__device__ __forceinline__ void drain_group(uint32_t (&v)[64], float gm, float (&tv)[kTopK], int (&ti)[kTopK],
+template <int G8, int CW>
+__device__ __forceinline__ void drain_group(uint32_t (&v)[CW], float gm, float (&tv)[kTopK], int (&ti)[kTopK],
                                             float &thr, float eps2, int cbase) {
     while (gm < thr) {
         int pos = 7;
@@ -221,20 +241,20 @@ __device__ __forceinline__ void drain_group(uint32_t (&v)[64], float gm, float (
         thr = admit_thr(tv, eps2);
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[8 * G8 + e] = (e == pos) ? __float_as_uint(CUDART_INF_F) : v[8 * G8 + e];
-        gm = min8<G8>(v);
+        gm = min8<G8, CW>(v);
     }
 }
 
-template <int G8>
-__device__ __forceinline__ void scan_groups(uint32_t (&v)[64], const float (&gm)[8], float (&tv)[kTopK],
+template <int G8, int CW>
+__device__ __forceinline__ void scan_groups(uint32_t (&v)[CW], const float (&gm)[CW / 8], float (&tv)[kTopK],
                                             int (&ti)[kTopK], float &thr, float eps2, int cbase) {
-    if constexpr (G8 < 8) {
-        if (gm[G8] < thr) drain_group<G8>(v, gm[G8], tv, ti, thr, eps2, cbase);
-        scan_groups<G8 + 1>(v, gm, tv, ti, thr, eps2, cbase);
+    if constexpr (G8 < CW / 8) {
+        if (gm[G8] < thr) drain_group<G8, CW>(v, gm[G8], tv, ti, thr, eps2, cbase);
+        scan_groups<G8 + 1, CW>(v, gm, tv, ti, thr, eps2, cbase);
     }
 }
 
-// Admission of one 64-column chunk whose minimum m beats the row's threshold.
+// Admission of one CW-column chunk whose minimum m beats the row's threshold.
 // Once m is in the list nothing at or above t1 = min(thr, m + 2 eps) can
 // enter, so the chunk matters only through its columns below t1. Column e
 // lies in row group e / 8 (minima gm) and in strided set e % 8 (minima sm);
@@ -243,16 +263,23 @@ __device__ __forceinline__ void scan_groups(uint32_t (&v)[64], const float (&gm)
 // Otherwise (a near-tie inside the chunk, or eps = 0) the groups are drained
 // one by one. Every lane runs the same instructions on the fast path, so a
 // warp pays for one admission per chunk however many of its rows have one.
-__device__ __forceinline__ void admit_chunk(uint32_t (&v)[64], const float (&gm)[8], float m, float (&tv)[kTopK],
+template <int CW>
+__device__ __forceinline__ void admit_chunk(uint32_t (&v)[CW], const float (&gm)[CW / 8], float m, float (&tv)[kTopK],
                                             int (&ti)[kTopK], float &thr, float eps2, int cbase) {
+    static_assert(CW == 32 || CW == 64, "chunks of 32 or 64 columns");
     const float t1 = fminf(thr, __fadd_ru(m, eps2));
     int na = 0, nb = 0, ga = 0, gb = 0;
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
-        const float sm = fmin3(fmin3(__uint_as_float(v[b]), __uint_as_float(v[b + 8]), __uint_as_float(v[b + 16])),
-                               fmin3(__uint_as_float(v[b + 24]), __uint_as_float(v[b + 32]), __uint_as_float(v[b + 40])),
-                               fminf(__uint_as_float(v[b + 48]), __uint_as_float(v[b + 56])));
-        const bool pa = gm[b] < t1, pb = sm < t1;
+        float sm;  // minimum of the strided set b, b + 8, b + 16, ...
+        if constexpr (CW == 64)
+            sm = fmin3(fmin3(__uint_as_float(v[b]), __uint_as_float(v[b + 8]), __uint_as_float(v[b + 16])),
+                       fmin3(__uint_as_float(v[b + 24]), __uint_as_float(v[b + 32]), __uint_as_float(v[b + 40])),
+                       fminf(__uint_as_float(v[b + 48]), __uint_as_float(v[b + 56])));
+        else
+            sm = fminf(fmin3(__uint_as_float(v[b]), __uint_as_float(v[b + 8]), __uint_as_float(v[b + 16])),
+                       __uint_as_float(v[b + 24]));
+        const bool pa = b < CW / 8 && gm[b < CW / 8 ? b : 0] < t1, pb = sm < t1;
         na += pa;
         ga += pa ? b : 0;
         nb += pb;
@@ -262,16 +289,37 @@ __device__ __forceinline__ void admit_chunk(uint32_t (&v)[64], const float (&gm)
         topk_insert<kTopK>(tv, ti, m, cbase + 8 * ga + gb);
         thr = admit_thr(tv, eps2);
     } else {
-        scan_groups<0>(v, gm, tv, ti, thr, eps2, cbase);
+        scan_groups<0, CW>(v, gm, tv, ti, thr, eps2, cbase);
     }
 }
 
-template <int G8>
-__device__ __forceinline__ void group_mins(const uint32_t (&v)[64], float (&gm)[8]) {
-    if constexpr (G8 < 8) {
-        gm[G8] = min8<G8>(v);
-        group_mins<G8 + 1>(v, gm);
+template <int G8, int CW>
+__device__ __forceinline__ void group_mins(const uint32_t (&v)[CW], float (&gm)[CW / 8]) {
+    if constexpr (G8 < CW / 8) {
+        gm[G8] = min8<G8, CW>(v);
+        group_mins<G8 + 1, CW>(v, gm);
     }
+}
+
+// One CW-column chunk of a row's scores into its running list: group minima,
+// the chunk minimum, and an admission when it beats the row's threshold.
+// Columns at or past P (the last tile's padding) count as +inf.
+template <int CW>
+__device__ __forceinline__ void epi_chunk(uint32_t (&v)[CW], int cbase, int P, bool full, float (&tv)[kTopK],
+                                          int (&ti)[kTopK], float &thr, float eps2) {
+    if (!full) {
+#pragma unroll
+        for (int e = 0; e < CW; ++e)
+            if (cbase + e >= P) v[e] = __float_as_uint(CUDART_INF_F);
+    }
+    float gm[CW / 8];
+    group_mins<0, CW>(v, gm);
+    float m;
+    if constexpr (CW == 64)
+        m = fmin3(fmin3(gm[0], gm[1], gm[2]), fmin3(gm[3], gm[4], gm[5]), fminf(gm[6], gm[7]));
+    else
+        m = fminf(fmin3(gm[0], gm[1], gm[2]), gm[3]);
+    if (m < thr) admit_chunk<CW>(v, gm, m, tv, ti, thr, eps2, cbase);
 }
 
 __device__ __forceinline__ uint32_t bf16_bits(__nv_bfloat16 h) { return (uint32_t)__bfloat16_as_ushort(h); }
@@ -723,26 +771,50 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
                         if ((int)(pb >> 32) == item)
                             thr[0] = fminf(thr[0], __fadd_ru(__uint_as_float((uint32_t)pb), eps2[0]));
                     }
-#pragma unroll 1
-                    for (int cc = 0; cc < HALF / 64; ++cc) {
-                        uint32_t v[64];
-                        __syncwarp();
-                        tmem_ld64(tmem + ((uint32_t)(q * 32) << 16) + col + (uint32_t)(cc * 64), v);
-                        const int cbase = j * C::BN + h * HALF + cc * 64;
-                        if (!full) {
-#pragma unroll
-                            for (int e = 0; e < 64; ++e)
-                                if (cbase + e >= P) v[e] = __float_as_uint(CUDART_INF_F);
-                        }
-                        float gm[8];
-                        group_mins<0>(v, gm);
-                        const float m =
-                            fmin3(fmin3(gm[0], gm[1], gm[2]), fmin3(gm[3], gm[4], gm[5]), fminf(gm[6], gm[7]));
-                        if (m < thr[0]) admit_chunk(v, gm, m, tv[0], ti[0], thr[0], eps2[0], cbase);
-                    }
+                    const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + col;
+                    const int cb0 = j * C::BN + h * HALF;
                     if constexpr (C::SEQ) {
+                        // 64-column chunks in one register buffer (two buffers would not
+                        // fit; 32-column slices in two buffers measured slower here)
+#pragma unroll 1
+                        for (int cc = 0; cc < HALF / 64; ++cc) {
+                            uint32_t v[64];
+                            __syncwarp();
+                            tmem_ld64(tbase + (uint32_t)(cc * 64), v);
+                            epi_chunk<64>(v, cb0 + cc * 64, P, full, tv[0], ti[0], thr[0], eps2[0]);
+                        }
                         tc_fence_before();
                         mbar_arrive(smem_u32(&sh.acc_empty[rbx]));
+                    } else {
+                        // 32-column slices in two register buffers: the next slice's TMEM
+                        // load is in flight while the current one is scanned, and the
+                        // accumulator is released once the last slice is in registers
+                        constexpr int NS = HALF / 32;
+                        static_assert(NS % 2 == 0, "slices come in pairs");
+                        uint32_t va[32], vb[32];
+                        __syncwarp();
+                        tmem_ld32(tbase, va);
+                        tmem_wait(va);
+#pragma unroll 1
+                        for (int sl = 0; sl < NS; sl += 2) {
+                            __syncwarp();
+                            tmem_ld32(tbase + (uint32_t)((sl + 1) * 32), vb);
+                            epi_chunk<32>(va, cb0 + sl * 32, P, full, tv[0], ti[0], thr[0], eps2[0]);
+                            __syncwarp();
+                            tmem_wait(vb);
+                            if (sl + 2 < NS) {
+                                tmem_ld32(tbase + (uint32_t)((sl + 2) * 32), va);
+                            } else if (rbx == RB - 1) {
+                                // every column of the accumulator has been read
+                                tc_fence_before();
+                                mbar_arrive(smem_u32(&sh.acc_empty[gacc & 1]));
+                            }
+                            epi_chunk<32>(vb, cb0 + (sl + 1) * 32, P, full, tv[0], ti[0], thr[0], eps2[0]);
+                            if (sl + 2 < NS) {
+                                __syncwarp();
+                                tmem_wait(va);
+                            }
+                        }
                     }
                     best[h] = ((unsigned long long)(uint32_t)item << 32) | __float_as_uint(tv[0][0]);
 #pragma unroll
@@ -761,12 +833,7 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
                     eps2[0] = eps2[1];
                     eps2[1] = se;
                 }
-                if constexpr (!C::SEQ) {
-                    if (ok) {
-                        tc_fence_before();
-                        mbar_arrive(smem_u32(&sh.acc_empty[gacc & 1]));
-                    }
-                }
+
             }
             if (!ok) break;
             // exchange halves: publish the list of row block 1-h (after the partner
