@@ -57,6 +57,7 @@ constexpr int UM = BM * RB;             // rows per unit
 constexpr int kEpiWarps = 8;                 // warps 4-11
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr unsigned long long kErrTcTimeout = 0x7C01;
+constexpr uint32_t kWaitHintNs = 100000;  // longest sleep of one try_wait (the bounded waits re-check)
 
 template <int N>
 struct TcCfg {
@@ -113,6 +114,20 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// try_wait with a suspend-time hint: a waiting thread sleeps until the phase
+// completes (or the hint runs out) instead of spinning, which leaves the issue
+// slots of its SM sub-partition to the warps that have work
+__device__ __forceinline__ bool mbar_try_sleep(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(kWaitHintNs)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -124,11 +139,9 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const vola
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 1; i < (1u << 30); ++i) {
-        if (mbar_try(bar, parity)) return true;
-        if ((i & 31u) == 0) {
-            if (*abort_flag) return false;
-            if (global_ns() - t0 > limit_ns) return false;
-        }
+        if (mbar_try_sleep(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
