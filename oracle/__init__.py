@@ -68,7 +68,7 @@ def _load():
             "or_scl": (i32, [P, P, i32, P, P]),
             "or_enumerate": (i64, [P, P, i32, P, i64]),
             "or_weight_distribution": (None, [P, P]),
-            "or_decode": (i32, [P, P, i64, i32, i32, i32, i32, i32, i32, P, P, P, P, P]),
+            "or_decode": (i32, [P, P, i64, i32, i32, i32, i32, i32, i32, P, P, P, P, P, P]),
             "or_osd": (i32, [P, P, i32, i32, P, P]),
             "or_mpwsd": (None, [P, P, P, i32, i32, P, P, P, P, P]),
             "or_ml": (None, [P, P, P, P]),
@@ -204,8 +204,11 @@ class Code:
     def decode(self, y, L: int, T: int, rule: int = RULE_TOP1, aom: bool = False, threads: int | None = None,
                want_anchors: bool = False, osd_order: int | None = None):
         """Two-stage decode of B frames (y: B x n). Returns a dict of numpy arrays:
-        cw (B x W uint64), flags (B uint16), min_gap (B float64), evals (B int64)
-        and, if asked, anchors (B x L x n bytes; rows past the list size are 0).
+        cw (B x W uint64), flags (B uint16), min_gap (B float64), evals (B int64),
+        evals_distinct (B int64: evals without the trajectories that hop onto the
+        centre of a lower-numbered one of their frame, which decide alike from
+        then on) and, if asked, anchors (B x L x n bytes; rows past the list size
+        are 0).
         Stage 1 is SC-list, or OSD(osd_order) when osd_order is given."""
         y = np.ascontiguousarray(y, np.float64).reshape(-1, self.n)
         B = y.shape[0]
@@ -213,15 +216,16 @@ class Code:
         flags = np.zeros(B, np.uint16)
         gap = np.zeros(B, np.float64)
         evals = np.zeros(B, np.int64)
+        evals_distinct = np.zeros(B, np.int64)
         anchors = np.zeros((B, L, self.n), np.uint8) if want_anchors else None
         if threads is None:
             threads = os.cpu_count() or 1
         rc = _load().or_decode(self._h, _ptr(y), B, L, T, rule, int(aom), -1 if osd_order is None else int(osd_order),
                                int(threads), _ptr(cw), _ptr(flags), _ptr(gap),
-                               _ptr(anchors) if anchors is not None else None, _ptr(evals))
+                               _ptr(anchors) if anchors is not None else None, _ptr(evals), _ptr(evals_distinct))
         if rc != 0:
             raise ValueError("oracle decode rejected its arguments")
-        out = dict(cw=cw, flags=flags, min_gap=gap, evals=evals)
+        out = dict(cw=cw, flags=flags, min_gap=gap, evals=evals, evals_distinct=evals_distinct)
         if anchors is not None:
             out["anchors"] = anchors
         return out

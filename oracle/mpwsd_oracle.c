@@ -408,6 +408,14 @@ typedef struct {
     int iters;           /* iterations of the outer loop that ran */
     double min_gap;      /* smallest ED gap between the chosen and the runner-up, over all decisions */
     int64_t evals;       /* (active trajectory, pattern) pairs scored by the filter */
+    /* The same count without retired twins. A trajectory is retired when, right
+     * after a hop, it sits on the centre of a live lower-numbered trajectory of
+     * the frame. Live means that trajectory hopped there in the same iteration
+     * or stopped there, and is not retired itself. From then on the two make
+     * the same decisions, or the row would stop next anyway, so the GPU scores
+     * only the lower one. This counts work only: nothing of the algorithm
+     * above changes. */
+    int64_t evals_distinct;
     int final_k;         /* winning path */
 } wsd_info;
 
@@ -452,13 +460,18 @@ static void mpwsd_frame(const or_code *c, const double *y, const uint8_t *anchor
     if (m > P) m = (int)P;
     uint8_t *ck = (uint8_t *)malloc((size_t)count * n + 1); /* current centres */
     uint8_t *active = (uint8_t *)malloc((size_t)count + 1);
+    uint8_t *retired = (uint8_t *)malloc((size_t)count + 1); /* not counted in evals_distinct */
     gain_ent *heap = (gain_ent *)malloc(sizeof(gain_ent) * (size_t)(m + 1));
     double xhat[OR_MAXN];
     memcpy(ck, anchors, (size_t)count * n);
-    for (int k = 0; k < count; k++) active[k] = 1;
+    for (int k = 0; k < count; k++) {
+        active[k] = 1;
+        retired[k] = 0;
+    }
     info->iters = 0;
     info->min_gap = INFINITY;
     info->evals = 0;
+    info->evals_distinct = 0;
     for (int it = 1; it <= J; it++) {
         int updated = 0;
         info->iters = it;
@@ -485,6 +498,7 @@ static void mpwsd_frame(const or_code *c, const double *y, const uint8_t *anchor
                 }
             }
             info->evals += P;
+            if (!retired[k]) info->evals_distinct += P;
             /* Search: exact squared Euclidean distance of every candidate in
              * M_k; ties keep the lowest pattern index. */
             double ed_cur = sq_dist(y, cur, n);
@@ -516,6 +530,11 @@ static void mpwsd_frame(const or_code *c, const double *y, const uint8_t *anchor
             }
             if (gap < info->min_gap) info->min_gap = gap;
         }
+        for (int k = 0; k < count; k++) {
+            if (!active[k] || retired[k]) continue;  /* only rows that hopped in this iteration */
+            for (int k2 = 0; k2 < k && !retired[k]; k2++)
+                if (!retired[k2] && memcmp(ck + (size_t)k2 * n, ck + (size_t)k * n, (size_t)n) == 0) retired[k] = 1;
+        }
         if (!updated) break;
     }
     /* Final decision: the path with the smallest ED; ties keep the lowest k. */
@@ -534,6 +553,7 @@ static void mpwsd_frame(const or_code *c, const double *y, const uint8_t *anchor
     info->final_k = bk;
     free(ck);
     free(active);
+    free(retired);
     free(heap);
 }
 
@@ -554,6 +574,7 @@ typedef struct {
     double *min_gap;    /* B, may be NULL */
     uint8_t *anchors_out; /* B x L x n, may be NULL: stage-1 list (u -> codewords) */
     int64_t *evals;     /* B, may be NULL */
+    int64_t *evals_distinct; /* B, may be NULL */
     int64_t next;       /* shared frame counter */
     pthread_mutex_t lock;
 } batch_job;
@@ -713,7 +734,8 @@ static void pack_bits(const uint8_t *b, int n, uint64_t *w) {
 /* Decode one frame. Flags: bit0 stage 2 ran, bit1 the output passes the CRC,
  * bits 4..7 outer iterations used by stage 2. */
 static void decode_frame(const or_code *c, const double *y, int L, int J, int rule, int aom, int osd_order,
-                         uint64_t *cw_out, uint16_t *flags, double *gap, uint8_t *anchors_out, int64_t *evals) {
+                         uint64_t *cw_out, uint16_t *flags, double *gap, uint8_t *anchors_out, int64_t *evals,
+                         int64_t *evals_distinct) {
     int n = c->n;
     uint8_t *ul = (uint8_t *)malloc((size_t)L * n);
     uint8_t *cl = (uint8_t *)malloc((size_t)L * n);
@@ -732,7 +754,7 @@ static void decode_frame(const or_code *c, const double *y, int L, int J, int ru
     }
     uint16_t fl = 0;
     double g = INFINITY;
-    int64_t ev = 0;
+    int64_t ev = 0, evd = 0;
     uint8_t out[OR_MAXN];
     int use_crc = (c->crc_len > 0) && !aom;
     int done = 0;
@@ -755,12 +777,14 @@ static void decode_frame(const or_code *c, const double *y, int L, int J, int ru
         fl |= (uint16_t)(it << 4);
         g = info.min_gap;
         ev = info.evals;
+        evd = info.evals_distinct;
     }
     if (crc_ok_codeword(c, out) && c->crc_len > 0) fl |= 2;
     pack_bits(out, n, cw_out);
     *flags = fl;
     if (gap) *gap = g;
     if (evals) *evals = ev;
+    if (evals_distinct) *evals_distinct = evd;
     free(ul); free(cl); free(pml);
 }
 
@@ -776,7 +800,7 @@ static void *batch_worker(void *arg) {
                      jb->flags + f,
                      jb->min_gap ? jb->min_gap + f : NULL,
                      jb->anchors_out ? jb->anchors_out + (size_t)f * jb->L * n : NULL,
-                     jb->evals ? jb->evals + f : NULL);
+                     jb->evals ? jb->evals + f : NULL, jb->evals_distinct ? jb->evals_distinct + f : NULL);
     }
     return NULL;
 }
@@ -785,12 +809,13 @@ static void *batch_worker(void *arg) {
  * means 1. Returns 0, or -1 on bad arguments. */
 int or_decode(const or_code *c, const double *y, int64_t B, int L, int J, int rule, int aom, int osd_order,
               int nthreads, uint64_t *cw_out, uint16_t *flags, double *min_gap, uint8_t *anchors_out,
-              int64_t *evals) {
+              int64_t *evals, int64_t *evals_distinct) {
     if (!c || L < 1 || J < 0 || B < 0) return -1;
     if (B == 0) return 0;
     batch_job jb;
     jb.c = c; jb.y = y; jb.B = B; jb.L = L; jb.J = J; jb.rule = rule; jb.aom = aom; jb.osd_order = osd_order;
     jb.cw_out = cw_out; jb.flags = flags; jb.min_gap = min_gap; jb.anchors_out = anchors_out; jb.evals = evals;
+    jb.evals_distinct = evals_distinct;
     jb.next = 0;
     pthread_mutex_init(&jb.lock, NULL);
     if (nthreads < 1) nthreads = 1;

@@ -108,11 +108,17 @@ __device__ __forceinline__ bool apply_decision(const Workspace &ws, const CodeDe
 
 enum RowOutcome { kRowNone = 0, kRowHop = 1, kRowStop = 2, kRowRescan = 3 };
 
-// Append trajectory t to the next active list (hop) or the rescan list, with
+// Active lists: iteration `iter` scores the rows of act[0] (count counters[1 +
+// iter]); the rows that hop go to act[1] (count counters[kHoppedBase + iter]),
+// and the duplicate retirement moves the distinct ones back into act[0] for
+// the next iteration.
+constexpr int kHoppedBase = 48;
+
+// Append trajectory t to the hopped list or the rescan list, with
 // warp-aggregated atomics; every lane of the warp calls this together.
 __device__ __forceinline__ void route_row(const Workspace &ws, int iter, int outcome, int t) {
-    const int po = append_slot(0xffffffffu, ws.counters + 1 + iter + 1, outcome == kRowHop);
-    if (po >= 0) ws.act[(iter + 1) & 1][po] = t;
+    const int po = append_slot(0xffffffffu, ws.counters + kHoppedBase + iter, outcome == kRowHop);
+    if (po >= 0) ws.act[1][po] = t;
     const int pr = append_slot(0xffffffffu, ws.counters + 32 + iter, outcome == kRowRescan);
     if (pr >= 0) ws.rescan_rows[pr] = t;
 }

@@ -26,6 +26,7 @@ constexpr float kEpsScale = 1.0f / 16384.0f;  // 2^-14
 constexpr uint32_t kTrajHopsMask = 0xffu;
 constexpr uint32_t kTrajRescan = 1u << 8;
 constexpr uint32_t kTrajValid = 1u << 9;
+constexpr uint32_t kTrajRetired = 1u << 10;  // dropped as the twin of a lower-numbered trajectory
 
 // Device-side counters (accumulated by the kernels; read by mpwsd_stats_get).
 struct DevStats {
@@ -177,6 +178,7 @@ bool score_tc_supported(const CodeDev &c);
 int rm_specialisation(int n, uint64_t lo, uint64_t hi);
 cudaError_t launch_hop(const CodeDev &c, const Workspace &ws, int iter, int L, const float *y, cudaStream_t s);
 cudaError_t launch_rescan(const CodeDev &c, const Workspace &ws, int iter, int L, const float *y, cudaStream_t s);
+cudaError_t launch_dedup(const CodeDev &c, const Workspace &ws, int iter, int L, cudaStream_t s);
 cudaError_t launch_final(const CodeDev &c, const Workspace &ws, int L, int T, int64_t B, uint64_t *cw_out, uint16_t *flags_out,
                          cudaStream_t s);
 

@@ -631,7 +631,7 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
     for (int it = 0; it < T; ++it) {
         ScoreArgs a{};
         a.y = y_dev;
-        a.rows = ws.act[it & 1];
+        a.rows = ws.act[0];
         a.n_rows_dev = ws.counters + 1 + it;
         a.cw = ws.traj_cw;
         a.slot_frame = ws.slot_frame;
@@ -650,6 +650,12 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
         if (e != cudaSuccess) return cuda_fail(e, "hop launch");
         e = timed_launch(code, MPWSD_KERNEL_RESCAN, s, [&] { return launch_rescan(d, ws, it, L, y_dev, s); });
         if (e != cudaSuccess) return cuda_fail(e, "rescan launch");
+        if (it + 1 < T) {
+            // the next iteration's rows: those that hopped, without duplicates of a
+            // lower-numbered trajectory of the same frame (counted with the hop class)
+            e = timed_launch(code, MPWSD_KERNEL_HOP, s, [&] { return launch_dedup(d, ws, it, L, s); });
+            if (e != cudaSuccess) return cuda_fail(e, "dedup launch");
+        }
     }
     e = timed_launch(code, MPWSD_KERNEL_FINAL, s, [&] { return launch_final(d, ws, L, T, B, cw_dev, flags_dev, s); });
     if (e != cudaSuccess) return cuda_fail(e, "final launch");

@@ -4,6 +4,9 @@
 //                  compaction of the rows still active (the only FP64 step);
 //   rescan_kernel  exact FP64 scan of every pattern for the rare rows whose
 //                  kept candidates could not prove the minimum (near-tie overflow);
+//   dedup_kernel   retirement of the trajectories that hopped onto the centre
+//                  of a lower-numbered trajectory of the same frame, and the
+//                  next iteration's active list;
 //   final_kernel   per failing frame, the trajectory of smallest ED (ties keep
 //                  the lowest anchor index), its CRC status and flags.
 #include "common.cuh"
@@ -26,7 +29,7 @@ constexpr int kHopThreads = 256;
 __global__ void __launch_bounds__(kHopThreads) hop_kernel(const Workspace ws, const CodeDev c, int iter, int L,
                                                           const float *y) {
     const int nrows = ws.counters[1 + iter];
-    const int *act_in = ws.act[iter & 1];
+    const int *act_in = ws.act[0];
     const int stride = gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     const int W = c.W, wq = c.wq_max, n = c.n;
@@ -112,8 +115,8 @@ __global__ void __launch_bounds__(kHopThreads) rescan_kernel(const Workspace ws,
     __shared__ double s_best[kHopThreads / 32];
     __shared__ int s_idx[kHopThreads / 32];
     const int nres = ws.counters[32 + iter];
-    int *act_out = ws.act[(iter + 1) & 1];
-    int *n_out = ws.counters + 1 + iter + 1;
+    int *act_out = ws.act[1];
+    int *n_out = ws.counters + kHoppedBase + iter;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = blockIdx.x; i < nres; i += gridDim.x) {
         const int t = ws.rescan_rows[i];
@@ -158,6 +161,51 @@ __global__ void __launch_bounds__(kHopThreads) rescan_kernel(const Workspace ws,
             }
         }
         __syncthreads();
+    }
+}
+
+// A row that has just hopped is retired when a lower-numbered trajectory of
+// its frame sits on the same centre and is itself live. Live means it hopped
+// onto that centre in this same iteration, or it stopped there. A twin that
+// hopped in the same iteration makes the same decisions from then on (a
+// decision depends on the centre and y alone) with the same hop count. A twin
+// that stopped proves that no improving pattern exists at that centre, so
+// the row would stop next time anyway. A retired trajectory's centre is stale
+// (its twin may have moved on), so it never serves as a twin. The retired row
+// keeps its centre, D and hop count, and the result is unchanged. The frame's
+// output is the smallest-ED trajectory (lowest anchor on ties), and a retired
+// row never beats its twin: its D is at least the twin's final D, and its
+// anchor is higher. The iteration count is the largest hop count plus one,
+// which the twin reaches as well. Flags written by this pass may or may not be
+// seen by other rows of the same pass; either way the outcome is the same,
+// because a row retired now has a live lower-numbered twin on the same centre,
+// and that twin serves every later row too.
+__global__ void __launch_bounds__(kHopThreads) dedup_kernel(const Workspace ws, const CodeDev c, int iter, int L) {
+    const int nrows = ws.counters[kHoppedBase + iter];
+    int *n_out = ws.counters + 1 + iter + 1;
+    const int stride = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const int W = c.W;
+    for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nrows; base += stride) {
+        const int r = base + lane;
+        bool keep = false;
+        int t = 0;
+        if (r < nrows) {
+            t = ws.act[1][r];
+            const int64_t first = (int64_t)(t / L) * L;
+            const uint64_t *cw = ws.traj_cw + (int64_t)t * W;
+            const uint64_t c0 = cw[0], c1 = W > 1 ? cw[1] : 0ull;
+            keep = true;
+            for (int64_t t2 = first; t2 < t && keep; ++t2) {
+                const uint32_t st2 = ws.traj_state[t2];
+                if (!(st2 & kTrajValid) || (st2 & kTrajRetired)) continue;
+                const uint64_t *cw2 = ws.traj_cw + t2 * W;
+                if (cw2[0] == c0 && (W == 1 || cw2[1] == c1)) keep = false;
+            }
+            if (!keep) ws.traj_state[t] |= kTrajRetired;
+        }
+        const int po = append_slot(0xffffffffu, n_out, keep);
+        if (po >= 0) ws.act[0][po] = t;
     }
 }
 
@@ -216,6 +264,11 @@ cudaError_t launch_hop(const CodeDev &c, const Workspace &ws, int iter, int L, c
 
 cudaError_t launch_rescan(const CodeDev &c, const Workspace &ws, int iter, int L, const float *y, cudaStream_t s) {
     rescan_kernel<<<c.num_sms * 2, kHopThreads, 0, s>>>(ws, c, iter, L, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dedup(const CodeDev &c, const Workspace &ws, int iter, int L, cudaStream_t s) {
+    dedup_kernel<<<c.num_sms * 4, kHopThreads, 0, s>>>(ws, c, iter, L);
     return cudaGetLastError();
 }
 

@@ -201,8 +201,11 @@ def test_stats_counters(mp, rm26, rm26_or):
     assert st["frames"] == 4000
     assert st["stage2_frames"] == int(np.sum(fl & 1))
     assert st["trajectories"] == 8 * st["stage2_frames"]
-    assert st["pattern_evals"] == int(ref["evals"].sum())
-    assert st["kernel_launches"] >= 1 + 3 * 4 + 1  # stage 1, T x (score, re-rank + hop, rescan), final
+    # rows the GPU scores: duplicates of a lower-numbered trajectory are retired
+    assert st["pattern_evals"] == int(ref["evals_distinct"].sum())
+    assert st["pattern_evals"] < int(ref["evals"].sum())
+    # stage 1, T x (score, re-rank + hop, rescan), T - 1 duplicate retirements, final
+    assert st["kernel_launches"] >= 1 + 3 * 4 + 3 + 1
 
 
 def test_graph_replay_matches_direct_launches(mp, rm26):

@@ -206,3 +206,55 @@ def test_gains_match_ed_differences(oracle_mod):
         G = code.gains(y, c)
         for p in (0, 7, 100, 2603):
             assert G[p] == (_ed(y, c) - _ed(y, c ^ P[p])) / 2
+
+
+def test_eval_counts_against_an_independent_emulation(oracle_mod):
+    """evals (every active (trajectory, pattern) pair of Algorithm 1) and
+    evals_distinct (the same without retired twins: rows that hopped onto the
+    centre of a live, unretired, lower-numbered trajectory) against a numpy
+    emulation of the stage-2 loop: exact scores of every pattern, argmin with
+    the lowest index on ties, a hop on a strictly negative score, stop when no
+    trajectory moved."""
+    import synth
+
+    code = oracle_mod.rm_code(6, 2, crc_poly=0x21, crc_len=6)
+    pats = code.enumerate_codewords([16])
+    code = code.with_patterns(pats)
+    P = oracle_mod.unpack_bits(pats, 64).astype(np.float64)
+    wl = synth.make_workload("rm26_crc6", 1.0, 120, seed=11)
+    L, T = 8, 4
+    out = code.decode(wl.y, L, T, threads=2, want_anchors=True)
+    twins = 0
+    for f in range(wl.y.shape[0]):
+        if not out["flags"][f] & 1:
+            assert out["evals"][f] == 0 and out["evals_distinct"][f] == 0
+            continue
+        y = wl.y[f].astype(np.float64)
+        ul, _ = code.scl(y, L)
+        cen = np.array([code.encode(u) for u in ul])
+        act = np.ones(len(cen), bool)
+        ret = np.zeros(len(cen), bool)
+        ev = evd = 0
+        for _ in range(T):
+            moved = False
+            for k in range(len(cen)):
+                if not act[k]:
+                    continue
+                ev += P.shape[0]
+                evd += 0 if ret[k] else P.shape[0]
+                s = P @ (y * (1.0 - 2.0 * cen[k]))
+                b = int(np.argmin(s))
+                if s[b] < 0:
+                    cen[k] ^= P[b].astype(np.uint8)
+                    moved = True
+                else:
+                    act[k] = False
+            for k in range(len(cen)):
+                if act[k] and not ret[k] and any(not ret[k2] and np.array_equal(cen[k2], cen[k]) for k2 in range(k)):
+                    ret[k] = True
+                    twins += 1
+            if not moved:
+                break
+        assert out["evals"][f] == ev, f
+        assert out["evals_distinct"][f] == evd, f
+    assert twins > 0  # the case the count exists for occurs in this sample
