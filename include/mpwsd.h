@@ -102,7 +102,9 @@ typedef struct mpwsd_stats {
     int64_t frames;            /* frames decoded */
     int64_t stage2_frames;     /* frames that ran stage 2 (P_act = stage2_frames / frames, Eq. (7)) */
     int64_t trajectories;      /* (frame, anchor) trajectories started */
-    int64_t pattern_evals;     /* (active trajectory, pattern) pairs scored, over all iterations */
+    int64_t pattern_evals;     /* (active trajectory, pattern) pairs scored, over all iterations; a
+                                  trajectory that hops onto the centre of a live lower-numbered one of
+                                  its frame is retired (same outputs) and no longer scored */
     int64_t rerank_candidates; /* candidates re-scored exactly in FP64 */
     int64_t rescans;           /* trajectories that needed a full FP64 rescan */
     int64_t hops;              /* strict-improvement moves taken */
@@ -309,7 +311,7 @@ MPWSD_API int mpwsd_sync(mpwsd_code *code, void *stream);
 #define MPWSD_KERNEL_SCL 0        /* stage 1: SC-list + CRC + compaction */
 #define MPWSD_KERNEL_SCORE_TC 1   /* scoring, tcgen05 BF16 hi+lo */
 #define MPWSD_KERNEL_SCORE_FP32 2 /* scoring, FP32 CUDA cores */
-#define MPWSD_KERNEL_HOP 3        /* FP64 near-tie re-rank + hop + compaction */
+#define MPWSD_KERNEL_HOP 3        /* FP64 near-tie re-rank + hop + compaction, and twin retirement */
 #define MPWSD_KERNEL_RESCAN 4     /* full FP64 rescan of overflowing rows */
 #define MPWSD_KERNEL_FINAL 5      /* per-frame argmin ED + flags */
 #define MPWSD_KERNEL_OSD 6        /* stage 1 by OSD(order) + CRC + compaction */
