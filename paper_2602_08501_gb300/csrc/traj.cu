@@ -195,14 +195,25 @@ __global__ void __launch_bounds__(kHopThreads) dedup_kernel(const Workspace ws, 
             const int64_t first = (int64_t)(t / L) * L;
             const uint64_t *cw = ws.traj_cw + (int64_t)t * W;
             const uint64_t c0 = cw[0], c1 = W > 1 ? cw[1] : 0ull;
-            keep = true;
-            for (int64_t t2 = first; t2 < t && keep; ++t2) {
-                const uint32_t st2 = ws.traj_state[t2];
-                if (!(st2 & kTrajValid) || (st2 & kTrajRetired)) continue;
-                const uint64_t *cw2 = ws.traj_cw + t2 * W;
-                if (cw2[0] == c0 && (W == 1 || cw2[1] == c1)) keep = false;
+            // the lower-numbered trajectories four at a time, their loads issued together
+            bool dup = false;
+            for (int64_t t2 = first; t2 < t; t2 += 4) {
+                uint32_t st2[4];
+                uint64_t a2[4], b2[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t x = t2 + u;
+                    const bool in = x < t;
+                    st2[u] = in ? ws.traj_state[x] : 0u;
+                    a2[u] = in ? ws.traj_cw[x * W] : 0ull;
+                    b2[u] = (in && W > 1) ? ws.traj_cw[x * W + 1] : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    dup |= (st2[u] & kTrajValid) && !(st2[u] & kTrajRetired) && a2[u] == c0 && b2[u] == c1;
             }
-            if (!keep) ws.traj_state[t] |= kTrajRetired;
+            keep = !dup;
+            if (dup) ws.traj_state[t] |= kTrajRetired;
         }
         const int po = append_slot(0xffffffffu, n_out, keep);
         if (po >= 0) ws.act[0][po] = t;
