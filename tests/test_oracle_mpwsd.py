@@ -258,3 +258,55 @@ def test_eval_counts_against_an_independent_emulation(oracle_mod):
         assert out["evals"][f] == ev, f
         assert out["evals_distinct"][f] == evd, f
     assert twins > 0  # the case the count exists for occurs in this sample
+
+
+def test_retiring_twins_changes_no_output():
+    """The GPU retires a trajectory that hops onto the centre of a live
+    (hopped in the same iteration, or stopped there, and not itself retired)
+    lower-numbered trajectory of its frame. Emulated here both ways on the
+    frames of a seeded batch: the chosen codeword (smallest ED, lowest anchor on
+    ties) and the iteration count (largest hop count + 1, at most T) agree."""
+    import oracle
+    import synth
+
+    code = oracle.rm_code(6, 2, crc_poly=0x21, crc_len=6)
+    pats = code.enumerate_codewords([16])
+    P = oracle.unpack_bits(pats, 64).astype(np.float64)
+    wl = synth.make_workload("rm26_crc6", 1.0, 150, seed=12)
+    L, T = 8, 4
+
+    def run(y, anchors, retire):
+        cen = anchors.copy()
+        act = np.ones(len(cen), bool)
+        ret = np.zeros(len(cen), bool)
+        hops = np.zeros(len(cen), int)
+        for _ in range(T):
+            for k in range(len(cen)):
+                if not act[k] or ret[k]:
+                    continue
+                s = P @ (y * (1.0 - 2.0 * cen[k]))
+                b = int(np.argmin(s))
+                if s[b] < 0:
+                    cen[k] ^= P[b].astype(np.uint8)
+                    hops[k] += 1
+                else:
+                    act[k] = False
+            if retire:
+                for k in range(len(cen)):
+                    if act[k] and not ret[k] and any(not ret[k2] and np.array_equal(cen[k2], cen[k]) for k2 in range(k)):
+                        ret[k] = True
+        ed = [float(np.sum((y - (1.0 - 2.0 * c)) ** 2)) for c in cen]
+        best = int(np.argmin(ed))  # first minimum: lowest anchor on ties
+        return cen[best].tolist(), min(T, int(hops.max()) + 1), int(ret.sum())
+
+    retired = 0
+    for y in wl.y.astype(np.float64):
+        ul, _ = code.scl(y, L)
+        anchors = np.array([code.encode(u) for u in ul])
+        if code.crc_ok(anchors[0]):
+            continue
+        a = run(y, anchors, False)
+        b = run(y, anchors, True)
+        assert a[:2] == b[:2]
+        retired += b[2]
+    assert retired > 0
