@@ -155,3 +155,27 @@ def test_osd_stage_one_decode_never_beats_ml_and_keeps_its_best_anchor(order):
         if out["flags"][f] & 1:  # stage 2 ran: the result is no worse than the best anchor
             ed_anchor = min(np.sum((y - (1.0 - 2.0 * a)) ** 2) for a in cl)
             assert ed <= ed_anchor + 1e-9
+
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_high_order_lists_hold_every_candidate_once(order):
+    """With L above the candidate count, OSD(order) returns sum_{i<=order}
+    C(k, i) entries: c0 xor (rows of F) for distinct sets F of independent
+    G_sys rows are distinct codewords. They come in ascending D, and every
+    entry's D matches the discrepancy computed here."""
+    import math
+
+    code = oracle.rm_code(6, 2)
+    F = oracle.kron_power(6)
+    fz = oracle.rm_frozen(6, 2)
+    k = int(np.sum(fz == 0))
+    expect = sum(math.comb(k, i) for i in range(order + 1))
+    rng = np.random.default_rng(20 + order)
+    y = synth.grid_quantize(rng.standard_normal(64) * 1.3).astype(np.float64)
+    cl, d = code.osd(y, order=order, L=expect + 5)
+    assert cl.shape[0] == expect
+    assert len({bytes(c) for c in cl}) == expect
+    assert all(_is_codeword(c, F, fz) for c in cl[:: max(1, expect // 200)])
+    assert np.all(np.diff(d) >= 0)
+    pick = rng.choice(expect, 50, replace=False)
+    assert np.array_equal(d[pick], np.array([_disc(y, cl[i]) for i in pick]))
