@@ -20,7 +20,42 @@ def to_words(cw_tensor) -> np.ndarray:
     return cw_tensor.cpu().numpy().view(np.uint64)
 
 
-FLAG_PARITY_MASK = 0x0001 | 0x0002 | 0x00F0  # stage2, crc ok, iterations (rescan bit is kernel-internal)
+# stage 2 ran, final CRC ok, iterations used, error (the oracle never sets it, so a
+# GPU error flag is a mismatch); the rescan bit (0x4) is kernel-internal
+FLAG_PARITY_MASK = 0x0001 | 0x0002 | 0x00F0 | 0x0100
+FLAG_ERROR = 0x0100
+TIE_REL = 1e-6  # a near tie: the oracle's smallest decision gap < 1e-6 ||y||^2 (squared ED)
+
+
+def excused_bound(frames: int) -> int:
+    """How many near-tie frames a parity check may excuse: one per 10^4 frames,
+    at least one. Both sides decide on exact integer sums of the 2^-19 grid, so
+    the expected count is 0; the bound keeps the tie exception from passing a
+    test vacuously when many frames are near ties."""
+    return max(1, frames // 10000)
+
+
+def assert_decode_parity(cw, fl, ref, y, label="", max_excused=None):
+    """GPU decode (cw: B x W uint64, fl: B uint16) against the oracle's ``ref``
+    on the frames y (B x n): codewords and flags bit-exact on every frame, the
+    error flag clear everywhere, and the only exceptions near-tie frames, at
+    most ``excused_bound(B)`` of them (listed in the failure message and
+    printed when any occur). Returns (excused frame indices, near-tie count)."""
+    y64 = np.asarray(y, np.float64)
+    B = y64.shape[0]
+    tie = ref["min_gap"] < TIE_REL * np.sum(y64 ** 2, axis=1)
+    err = np.flatnonzero(fl & FLAG_ERROR)
+    assert err.size == 0, f"{label}: error flag on {err.size} frames, first {err[:10].tolist()}"
+    bad = np.flatnonzero(np.any(cw != ref["cw"], axis=1) | ((fl & FLAG_PARITY_MASK) != (ref["flags"] & FLAG_PARITY_MASK)))
+    outside = bad[~tie[bad]]
+    assert outside.size == 0, (f"{label}: {outside.size} frames differ from the oracle away from any near tie, "
+                               f"first {outside[:10].tolist()}")
+    bound = excused_bound(B) if max_excused is None else max_excused
+    assert bad.size <= bound, (f"{label}: {bad.size} near-tie frames differ (at most {bound} may be excused): "
+                               f"{bad[:50].tolist()}")
+    if bad.size:
+        print(f"{label}: excused near-tie frames {bad.tolist()} of {B} ({int(tie.sum())} near ties)")
+    return bad, int(tie.sum())
 
 
 def oracle_code(oracle_mod, m, r, crc_len, weights):

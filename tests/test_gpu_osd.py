@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_common import FLAG_PARITY_MASK, cuda_or_skip, oracle_code, to_words, torch
+from gpu_common import assert_decode_parity, cuda_or_skip, oracle_code, to_words, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -73,9 +73,7 @@ def _decode_parity(mp, code, ocode, y, L, T, order, mode, aom=False):
     torch.cuda.synchronize()
     cw, fl = to_words(cw), fl.cpu().numpy().view(np.uint16)
     ref = ocode.decode(y, L, T, aom=aom, osd_order=order)
-    tie = ref["min_gap"] < 1e-6 * np.sum(y.astype(np.float64) ** 2, axis=1)
-    bad = np.flatnonzero(np.any(cw != ref["cw"], axis=1) | ((fl & FLAG_PARITY_MASK) != (ref["flags"] & FLAG_PARITY_MASK)))
-    assert set(bad.tolist()) <= set(np.flatnonzero(tie).tolist()), (bad[:10], tie.sum())
+    assert_decode_parity(cw, fl, ref, y, label=f"OSD({order}) L={L} T={T} {mode} aom={aom}")
     return fl
 
 
@@ -94,6 +92,34 @@ def test_decode_with_osd_anchors_rm27(mp, oracle_mod):
     ocode = oracle_code(oracle_mod, 7, 2, 6, [32])
     wl = synth.make_workload("rm27_crc6", 1.5, 200, seed=54)
     _decode_parity(mp, code, ocode, wl.y, 16, 6, 2, "bf16x2")
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_decode_rm128_29_always_on(mp, oracle_mod, order):
+    """The paper's RM experiment (Sec. IV-C, Sec. III-C always-on mode):
+    RM(128, 29) with no CRC, stage 2 on every frame, OSD(order) anchors, J = 4,
+    the 10,668 weight-32 patterns; bit-exact against the oracle."""
+    code = mp.Code.rm(7, 2, weights=[32])
+    ocode = oracle_code(oracle_mod, 7, 2, 0, [32])
+    wl = synth.make_workload("rm27", 1.0, 400, seed=60 + order)
+    fl = _decode_parity(mp, code, ocode, wl.y, 16, 4, order, "bf16x2", aom=True)
+    assert np.all(fl & 1) and not np.any(fl & 2)  # no CRC: stage 2 ran everywhere, no CRC-ok flag
+    # with no CRC the stage-1 exit cannot happen, so the always-on switch changes nothing
+    cw2, fl2 = code.decode(_dev(wl.y), 16, 4, osd_order=order)
+    cw1, fl1 = code.decode(_dev(wl.y), 16, 4, osd_order=order, always_on=True)
+    torch.cuda.synchronize()
+    assert torch.equal(cw1, cw2) and torch.equal(fl1, fl2)
+    if order == 2:
+        _decode_parity(mp, code, ocode, wl.y[:120], 16, 4, order, "fp32", aom=True)
+
+
+def test_decode_rm128_29_always_on_list_sizes(mp, oracle_mod):
+    """The same pipeline with 1, 8 and 32 anchors and a single iteration."""
+    code = mp.Code.rm(7, 2, weights=[32])
+    ocode = oracle_code(oracle_mod, 7, 2, 0, [32])
+    wl = synth.make_workload("rm27", 0.5, 150, seed=66)
+    for L, T in ((1, 4), (8, 1), (32, 4)):
+        _decode_parity(mp, code, ocode, wl.y, L, T, 3, "bf16x2", aom=True)
 
 
 def test_osd_options_are_validated(mp):

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_common import cuda_or_skip, oracle_code, to_words, torch
+from gpu_common import FLAG_PARITY_MASK, cuda_or_skip, oracle_code, to_words, torch
 from test_gpu_parity import _decode_parity, _dev, _score_case
 
 pytestmark = pytest.mark.gpu
@@ -72,7 +72,7 @@ def test_decode_parity_cfg1_bf16x2(mp, rm26, rm26_or, ebn0):
     cw2, fl2 = rm26.decode(_dev(wl.y), 8, 4, score_mode="fp32")
     torch.cuda.synchronize()
     assert np.array_equal(cw, to_words(cw2))
-    assert np.array_equal(fl & 0xF3, fl2.cpu().numpy().view(np.uint16) & 0xF3)
+    assert np.array_equal(fl & FLAG_PARITY_MASK, fl2.cpu().numpy().view(np.uint16) & FLAG_PARITY_MASK)
 
 
 def test_decode_edge_cases_bf16x2(mp, rm26, rm26_or):
@@ -88,17 +88,23 @@ def test_decode_edge_cases_bf16x2(mp, rm26, rm26_or):
             _decode_parity(mp, rm26, rm26_or, sub, L, T, "bf16x2", aom=aom)
 
 
-def test_decode_rm27_bf16x2(mp, oracle_mod):
+@pytest.mark.parametrize("ebn0", [0.5, 1.5, 2.5])
+def test_decode_rm27_bf16x2(mp, oracle_mod, ebn0):
+    """RM(2,7)+CRC-6 at each Eb/N0 of its workload, L = 16, T = 6, 10668 weight-32
+    patterns (oracle-sized samples of the seed-2 stream)."""
     code = mp.Code.rm(7, 2, crc_poly=0x21, crc_len=6, weights=[32])
     ocode = oracle_code(oracle_mod, 7, 2, 6, [32])
-    wl = synth.make_workload("rm27_crc6", 1.5, 400, seed=2)
-    _decode_parity(mp, code, ocode, wl, 16, 6, "bf16x2")
+    wl = synth.make_workload("rm27_crc6", ebn0, 400, seed=2)
+    _, fl, _ = _decode_parity(mp, code, ocode, wl, 16, 6, "bf16x2")
+    assert np.any(fl & 1)
 
 
 def test_decode_cfg4_patterns_bf16x2(mp, oracle_mod):
-    """Weight-16 and weight-24 patterns (294,252), L = 32, T = 8 on an oracle-sized sample."""
+    """Weight-16 and weight-24 patterns (294,252), L = 32, T = 8 on 400 frames of
+    the seed-3 stream at 0.5 dB; both scoring forms."""
     code = mp.Code.rm(6, 2, crc_poly=0x21, crc_len=6, weights=[16, 24])
     ocode = oracle_code(oracle_mod, 6, 2, 6, [16, 24])
-    wl = synth.make_workload("rm26_crc6", 0.5, 24, seed=3)
-    _decode_parity(mp, code, ocode, wl, 32, 8, "bf16x2")
+    wl = synth.make_workload("rm26_crc6", 0.5, 400, seed=3)
+    _, fl, _ = _decode_parity(mp, code, ocode, wl, 32, 8, "bf16x2")
+    assert np.sum(fl & 1) >= 100
     _decode_parity(mp, code, ocode, wl, 32, 8, "fp32")

@@ -97,7 +97,7 @@ def test_full_list_is_codebook_with_bruteforce_metrics(oracle_mod):
         assert np.all(np.diff(pm) >= 0)
 
 
-def test_list_sorted_and_contains_sc_path(oracle_mod):
+def test_list_sorted_distinct_and_frozen_zero(oracle_mod):
     code = oracle_mod.rm_code(6, 2)
     ys, _ = _noisy_frames(oracle_mod, code, 20, 1.2, seed=5)
     for y in ys:
@@ -108,6 +108,56 @@ def test_list_sorted_and_contains_sc_path(oracle_mod):
             assert len({tuple(u) for u in ul.tolist()}) == L
             # frozen positions are zero in every path
             assert not ul[:, code.frozen.astype(bool)].any()
+
+
+def leaf_llrs_ref(lam, u):
+    """Recursive SC with every decision imposed by u: (codeword of the block,
+    LLR seen at each leaf). Written like ``sc_ref``, independently of the oracle."""
+    if len(lam) == 1:
+        return [int(u[0])], [lam[0]]
+    h = len(lam) // 2
+    a, b = lam[:h], lam[h:]
+    cL, lL = leaf_llrs_ref([_f(x, y) for x, y in zip(a, b)], u[:h])
+    cR, lR = leaf_llrs_ref([y + (1 - 2 * c) * x for x, y, c in zip(a, b, cL)], u[h:])
+    return [p ^ q for p, q in zip(cL, cR)] + cR, lL + lR
+
+
+def scl_breadth_first_ref(lam, frozen, L):
+    """SC-list by its definition: every surviving path is extended leaf by
+    leaf; at an information leaf each path spawns both bits, the metric grows
+    by |lambda| when the bit disagrees with the hard decision, and the L best
+    children are kept in the order (metric, parent position, bit); a frozen leaf
+    takes 0 and keeps the order; the final list is stably sorted by metric.
+    Each leaf LLR comes from a fresh recursive SC pass over the path's prefix."""
+    n = len(lam)
+    paths = [([], 0.0)]
+    for i in range(n):
+        children = []
+        for q, (u, pm) in enumerate(paths):
+            li = leaf_llrs_ref(lam, u + [0] * (n - len(u)))[1][i]
+            hd = 0 if li >= 0 else 1
+            for bit in ((0,) if frozen[i] else (0, 1)):
+                children.append((u + [bit], pm + (abs(li) if bit != hd else 0.0), q, bit))
+        if not frozen[i]:
+            children.sort(key=lambda t: (t[1], t[2], t[3]))
+            children = children[:L]
+        paths = [(t[0], t[1]) for t in children]
+    paths.sort(key=lambda t: t[1])
+    return paths
+
+
+@pytest.mark.parametrize("m,r,Ls,frames", [(5, 1, (2, 3, 8, 32), 8), (6, 2, (2, 4, 8, 16), 5), (7, 2, (16,), 2)])
+def test_list_equals_breadth_first_reference(oracle_mod, m, r, Ls, frames):
+    """1 < L < 2^k, where pruning decides what survives: the oracle's list
+    (paths and metrics, in order) equals the breadth-first reference."""
+    code = oracle_mod.rm_code(m, r)
+    ys, _ = _noisy_frames(oracle_mod, code, frames, 1.3, seed=40 + m)
+    for y in ys:
+        for L in Ls:
+            ul, pm = code.scl(y, L)
+            want = scl_breadth_first_ref(list(y), list(code.frozen), L)
+            assert [list(u) for u in ul.tolist()] == [p[0] for p in want], (m, L)
+            assert pm.tolist() == [p[1] for p in want], (m, L)
 
 
 def test_noiseless_frame_decodes_with_zero_metric(oracle_mod):
