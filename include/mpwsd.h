@@ -228,18 +228,26 @@ MPWSD_API int mpwsd_decode_ws(mpwsd_code *code, mpwsd_workspace *ws, const float
 /*
  * mpwsd_decode_noalloc -- mpwsd_decode for callers that cannot allocate device
  * memory when they decode. The paper has no counterpart: this is an interface
- * of the library. Typical such callers record their work into a CUDA graph
- * (cudaMalloc is not allowed while a stream is being captured), run serving
- * threads that must not call an allocator once warmed up, or live in a host
- * whose device memory belongs to an allocator the library must not bypass.
+ * of the library. Such callers include serving threads that must not call an
+ * allocator once warmed up (an allocation can block or fail at an arbitrary
+ * moment), and hosts whose device memory belongs to an allocator that the
+ * library must not bypass (a framework's pool that owns the GPU's memory).
  *
  * Same arguments and results as mpwsd_decode; the caller still provides y_dev,
  * cw_dev and flags_dev. The scratch is one fixed 4 MiB array in device memory
  * that every GPU loading the library keeps until the process exits; this
  * entry point never calls cudaMalloc, cudaFree or any allocating routine.
- *  - Capacity: B frames with list size L must fit in 4 MiB of scratch (about
- *    43,000 (L = 8) to 58,000 (L = 32) trajectories B*L); larger requests return MPWSD_EINVAL
+ *  - Capacity: a call needs 4n + 8 bytes per frame and 8W + 56 bytes per
+ *    trajectory (W = n/64 words per codeword), each array rounded up to 256
+ *    bytes, plus 256 bytes of counters. So 4 MiB holds about
+ *    4 MiB / (4n + 8 + L (8W + 56)) frames: about 5,400 frames (43,000
+ *    trajectories B*L) for n = 64, L = 8; about 2,500 frames (40,000
+ *    trajectories) for n = 128, L = 16. Larger requests return MPWSD_EINVAL
  *    with the sizes in mpwsd_last_error().
+ *  - Speed: the scratch holds no room for the pattern split of the
+ *    tensor-core scoring kernel (MPWSD_TUNE_SPLIT_ITEMS), so small batches
+ *    score without it and can run slower than through mpwsd_decode; the
+ *    results are identical.
  *  - Set-up: the first call on each device (with that device current) looks
  *    up the array's device address; make that first call before any stream
  *    capture begins.

@@ -1084,12 +1084,13 @@ extern "C" int mpwsd_enumerate_codewords(int n, const uint8_t *frozen, const int
 
 // ---- allocation-free decode ---------------------------------------------------
 //
-// Some callers cannot allocate device memory at decode time: code running
-// while a CUDA stream is being captured into a graph (cudaMalloc is not
-// allowed there), serving threads that must not touch the allocator once
-// warmed up, and hosts whose device memory is owned by another allocator that
-// the library must not bypass. For them, mpwsd_decode_noalloc runs the same
-// decode with its scratch in one file-scope device array of fixed size.
+// Some callers cannot allocate device memory at decode time: serving threads
+// that must not touch the allocator once warmed up, and hosts whose device
+// memory is owned by another allocator that the library must not bypass. For
+// them, mpwsd_decode_noalloc runs the same decode with its scratch in one
+// file-scope device array of fixed size. The array holds the workspace layout
+// only; the pattern split of the scoring kernel has no buffers there, so this
+// path scores without it (same results).
 
 namespace {
 

@@ -14,6 +14,7 @@ from .channel import (  # noqa: F401
     make_workload,
     pack_bits,
     rm_info_set,
+    shard_batches,
     sigma_for,
     splitmix64_stream,
 )

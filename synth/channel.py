@@ -124,7 +124,15 @@ CODES = {
     "rm26_crc6": dict(m=6, r=2, crc_poly=0x21, crc_len=6),
     "rm27_crc6": dict(m=7, r=2, crc_poly=0x21, crc_len=6),
     "rm26": dict(m=6, r=2, crc_poly=0x0, crc_len=0),
+    # RM(128, 29) with no CRC: all 29 information bits carry the message
+    "rm27": dict(m=7, r=2, crc_poly=0x0, crc_len=0),
 }
+
+
+def shard_batches(total_batches: int, world: int, rank: int) -> list:
+    """Batches of one stream dealt round-robin over ranks: batch b goes to
+    rank b mod world. Returns the batch numbers of ``rank``."""
+    return list(range(rank, total_batches, world))
 
 
 @dataclass

@@ -1,6 +1,6 @@
-"""The multi-rank path of bench.py on CPU: two gloo ranks, each with its own
-frame shard; the timer reduction takes the max over ranks and the work the
-sum (no data-path collective)."""
+"""The multi-rank path of bench.py on CPU: gloo ranks, each with its own batch
+of one seeded frame stream (batch b on rank b mod N); the timer reduction
+takes the max over ranks and the work the sum (no data-path collective)."""
 import os
 import socket
 
@@ -24,19 +24,25 @@ def _worker(rank, world, port, q):
 
     red = bench.RankReduce(dist, "cpu")
     red.barrier()
-    seed = bench.rank_seed(1, rank)
-    wl = synth.make_workload("rm26_crc6", 1.0, 64, seed=seed)
+    first = bench.rank_first_frame(B, world, rank)
+    wl = synth.make_workload("rm26_crc6", 1.0, B, seed=1, first_frame=first)
     mx = red.max(10.0 + rank)
     sm = red.sum(100 * (rank + 1))
-    q.put((rank, seed, wl.y[:2].tolist(), mx, sm))
+    q.put((rank, first, wl.y.tolist(), mx, sm))
     dist.destroy_process_group()
 
 
-def test_two_rank_reduction_and_disjoint_shards():
+B = 48  # frames per rank and step
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_rank_reduction_and_round_robin_batches(world):
+    import synth
+
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
     for p in procs:
         p.start()
     res = [q.get(timeout=120) for _ in procs]
@@ -44,7 +50,22 @@ def test_two_rank_reduction_and_disjoint_shards():
         p.join(timeout=60)
         assert p.exitcode == 0
     res.sort()
-    assert [r[1] for r in res] == [1, 2]
-    assert not np.array_equal(np.array(res[0][2]), np.array(res[1][2]))
-    assert all(r[3] == 11.0 for r in res)
-    assert all(r[4] == 300.0 for r in res)
+    # batch b of the stream on rank b mod world: disjoint frame ranges that tile [0, world B)
+    assert [r[1] for r in res] == [B * r for r in range(world)]
+    stream = synth.make_workload("rm26_crc6", 1.0, world * B, seed=1)
+    assert np.array_equal(np.concatenate([np.array(r[2], np.float32) for r in res]), stream.y)
+    # rank 0 decodes the frames a one-rank run decodes
+    assert np.array_equal(np.array(res[0][2], np.float32), synth.make_workload("rm26_crc6", 1.0, B, seed=1).y)
+    assert all(r[3] == 10.0 + world - 1 for r in res)
+    assert all(r[4] == 100 * world * (world + 1) // 2 for r in res)
+
+
+def test_shard_batches_partitions():
+    import synth
+
+    for total in (1, 5, 12):
+        for world in (1, 2, 3, 8):
+            parts = [synth.shard_batches(total, world, r) for r in range(world)]
+            flat = sorted(b for p in parts for b in p)
+            assert flat == list(range(total))
+            assert all(b % world == r for r, p in enumerate(parts) for b in p)

@@ -1,9 +1,9 @@
 """The allocation-free decode entry point (mpwsd_decode_noalloc).
 
 Callers that cannot allocate device memory at decode time use this entry point:
-work being recorded into a CUDA graph, serving threads that must not touch an
-allocator after warm-up, and hosts whose device memory belongs to another
-allocator. It must return exactly what mpwsd_decode returns on the same
+serving threads that must not touch an allocator after warm-up, and hosts whose
+device memory belongs to another allocator (a framework's pool that owns the
+GPU's memory). It must return exactly what mpwsd_decode returns on the same
 inputs, call after call, although every call reuses one fixed scratch array.
 This file is collected last on purpose, and it passes both alone in a fresh
 process and after the other tests.
