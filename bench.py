@@ -60,7 +60,7 @@ WORKLOADS = {
                           desc="RM(2,6)+CRC-6, Eb/N0 {ebn0} dB, {frames} frames, seed {seed}, L=32, T=8, "
                                "294252 w16+w24 patterns"),
 }
-# The paper's RM experiment (Sec. IV-C, Table II): RM(128, 29) with no CRC, stage 2
+# The paper's RM experiment (Sec. IV-A settings, Table II): RM(128, 29) with no CRC, stage 2
 # always on (P_act = 1, Sec. III-C), OSD(order) anchors, J = 4, the r = 1 sphere
 # (the 10,668 weight-32 codewords). The list size and Eb/N0 are not printed in
 # the text; L = 16 and 1 dB (oracle FER about 2.5 %) are this workload's choice.

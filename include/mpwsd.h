@@ -73,7 +73,7 @@ extern "C" {
 
 #define MPWSD_STAGE1_SCL 0      /* stage 1 = min-sum SC-list decoding (Sec. III-A) */
 #define MPWSD_STAGE1_OSD 1      /* stage 1 = ordered-statistics decoding OSD(osd_order), the anchors of the RM
-                                   experiment (Sec. IV-C); needs k <= 32 */
+                                   experiment (Sec. IV-A); needs k <= 32 */
 #define MPWSD_MAX_OSD_ORDER 4
 
 /* Output flag bits (one uint16 per frame). */

@@ -15,7 +15,7 @@
  *   - stage 1: list decoding, CRC on the most reliable
  *     candidate, early termination .......................... Sec. III-A
  *   - stage 1 alternative: ordered-statistics decoding
- *     OSD(order) as the anchor list (the RM experiment) ..... Sec. IV-C
+ *     OSD(order) as the anchor list (the RM experiment) ..... Sec. IV-A
  *   - stage 2: MP-WSD update Eq. (4), Algorithm 1 with the
  *     top-m filter by the correlation gain of Eq. (5) and the
  *     exact-ED search, strict-improvement hop, final argmin ... Sec. III-B/C
@@ -580,7 +580,7 @@ typedef struct {
 } batch_job;
 
 /* ------------------------------------------------------------------------ */
-/* Stage 1 alternative: OSD(order) list (Sec. IV-C uses OSD(2) anchors)       */
+/* Stage 1 alternative: OSD(order) list (Sec. IV-A uses OSD anchors)            */
 /* ------------------------------------------------------------------------ */
 /* The paper names OSD without details; this is the standard construction:
  *  1. hard decisions hd_j = [y_j < 0] and reliabilities |y_j|;

@@ -1,5 +1,5 @@
 // Stage 1 by ordered-statistics decoding, OSD(order): the anchor list of the
-// RM experiment (Sec. IV-C; the paper names OSD without details, this is the
+// RM experiment (Sec. IV-A; the paper names OSD without details, this is the
 // standard construction). For each frame:
 //   1. hard decisions hd_j = [y_j < 0], reliabilities |y_j| on the 2^-19 grid;
 //   2. positions in decreasing reliability, ties to the lower index;

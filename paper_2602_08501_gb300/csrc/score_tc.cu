@@ -475,7 +475,10 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
     } else if (warp == 1) {
         // ---- MMA issuer (issue order per n: see the file comment) ----
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(BM, C::BN);
+            constexpr uint32_t idesc_full = idesc_bf16(BM, C::BN);
+            // the last tile holds P - (nt - 1) BN patterns: its MMAs are only as wide
+            // as those, rounded up to the MMA's N granularity of 16 (M = 128)
+            const uint32_t idesc_last = idesc_bf16(BM, min(C::BN, ((P - (nt - 1) * C::BN) + 15) & ~15));
             int gb = 0, gacc = 0;
             bool ok = true;
             uint32_t last_bar = 0, last_par = 0;
@@ -496,6 +499,7 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
                         break;
                     }
                     const uint32_t bsm = smem_u32(Bbase + s * C::B_STAGE_BYTES);
+                    const uint32_t idesc = j == nt - 1 ? idesc_last : idesc_full;
                     if constexpr (C::SEQ) {
                         for (int rb = 0; rb < RB; ++rb) {
                             if (!mbar_wait(smem_u32(&sh.acc_empty[rb]), ((uint32_t)gacc & 1u) ^ 1u, abort_flag,
@@ -791,6 +795,8 @@ __global__ void __launch_bounds__(TcCfg<N>::THREADS, 1) score_tc_kernel(const Sc
                         // fit; 32-column slices in two buffers measured slower here)
 #pragma unroll 1
                         for (int cc = 0; cc < HALF / 64; ++cc) {
+                            // columns past P hold nothing (the last tile's MMAs are narrower)
+                            if (cb0 + cc * 64 >= P) break;
                             uint32_t v[64];
                             __syncwarp();
                             tmem_ld64(tbase + (uint32_t)(cc * 64), v);

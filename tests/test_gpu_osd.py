@@ -96,7 +96,7 @@ def test_decode_with_osd_anchors_rm27(mp, oracle_mod):
 
 @pytest.mark.parametrize("order", [2, 3, 4])
 def test_decode_rm128_29_always_on(mp, oracle_mod, order):
-    """The paper's RM experiment (Sec. IV-C, Sec. III-C always-on mode):
+    """The paper's RM experiment (Sec. IV-A settings, Sec. III-C always-on mode):
     RM(128, 29) with no CRC, stage 2 on every frame, OSD(order) anchors, J = 4,
     the 10,668 weight-32 patterns; bit-exact against the oracle."""
     code = mp.Code.rm(7, 2, weights=[32])

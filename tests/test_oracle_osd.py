@@ -1,4 +1,4 @@
-"""Pins of the oracle's OSD(order) stage 1 (Sec. IV-C uses OSD anchors for the
+"""Pins of the oracle's OSD(order) stage 1 (Sec. IV-A uses OSD anchors for the
 RM code): each check uses something other than the oracle itself -- brute
 force over the whole code, the ED identity, a GF(2) rank computation written
 here, and frames whose answer is known by construction."""
