@@ -113,6 +113,7 @@ typedef struct mpwsd_stats {
 
 typedef struct mpwsd_code mpwsd_code;           /* opaque, owned by the library */
 typedef struct mpwsd_workspace mpwsd_workspace; /* opaque, owned by the library */
+typedef struct mpwsd_pool mpwsd_pool;           /* opaque, owned by the library */
 
 /* Human-readable name of a status code (static storage). */
 MPWSD_API const char *mpwsd_strerror(int status);
@@ -224,6 +225,78 @@ MPWSD_API int mpwsd_workspace_bytes(const mpwsd_code *code, int64_t max_B, int m
 /* mpwsd_decode with a caller-provided workspace (B <= its max_B, L <= its max_L). */
 MPWSD_API int mpwsd_decode_ws(mpwsd_code *code, mpwsd_workspace *ws, const float *y_dev, int64_t B, int L, int T,
                     const mpwsd_opts *opts, uint64_t *cw_dev, uint16_t *flags_dev, void *stream);
+
+/*
+ * Continuous stage-2 batching (pools). Algorithm 1 (Sec. III-B) treats each
+ * trajectory on its own, and each iteration of its loop depends only on the
+ * trajectory's current centre, so trajectories of frames that arrived at
+ * different times can share one scoring pass. A pool holds the stage-2 state
+ * of one code between calls: mpwsd_pool_submit runs stage 1 (Sec. III-A) on a
+ * batch, writes the frames that pass the CRC at once, and adds the L
+ * trajectories of every failing frame to the pool's rows; mpwsd_pool_step runs
+ * one iteration of Algorithm 1 on all rows of the pool (score every pattern,
+ * exact re-rank, strict-improvement hop, twin retirement), then, for each frame
+ * whose trajectories have all ended (stopped, made T hops, or retired), the
+ * final choice of Algorithm 1 (smallest ED, lowest anchor on ties) into that
+ * frame's output entries, and frees its slot. Every result equals what
+ * mpwsd_decode returns for the frame, whatever it was batched with.
+ * The paper has no counterpart for the pool itself: it is an interface of the
+ * library for serving.
+ *
+ * Calls on one pool must be ordered on the device (one stream, or events);
+ * the pool's device state is read and written by every call. Several pools
+ * (one per code, or several per code) can run on different streams at once.
+ */
+
+/*
+ * mpwsd_pool_create -- a pool of max_frames frame slots for lists of L anchors
+ * and at most T iterations. opts as in mpwsd_decode (scoring form, stage-1
+ * rule and kind, always-on; use_graph records the step's launches into a CUDA
+ * graph on the first step and replays it). One cudaMalloc holds everything;
+ * MPWSD_ENOMEM when device memory is short.
+ */
+MPWSD_API int mpwsd_pool_create(mpwsd_code *code, int64_t max_frames, int L, int T, const mpwsd_opts *opts,
+                                mpwsd_pool **out);
+
+/* Release a pool (waits for the device). NULL is a no-op. */
+MPWSD_API void mpwsd_pool_free(mpwsd_pool *pool);
+
+/* Bytes of device memory a pool of (max_frames, L) takes (no allocation). */
+MPWSD_API int mpwsd_pool_bytes(const mpwsd_code *code, int64_t max_frames, int L, size_t *bytes);
+
+/*
+ * mpwsd_pool_free_frames -- how many frames the next submission may carry. A
+ * submission's frames have all finished T steps after it, so the pool counts
+ * every frame of the submissions of the last T steps as in flight (whether or
+ * not it passed stage 1); no device read-back is involved.
+ */
+MPWSD_API int mpwsd_pool_free_frames(const mpwsd_pool *pool, int64_t *frames);
+
+/*
+ * mpwsd_pool_submit -- stage 1 on B frames; their trajectories join the pool.
+ *
+ *   y_dev      device, B x n FP32 (read by this call's stage-1 kernel only: it
+ *              may be overwritten once the stream has passed this call).
+ *   cw_dev     device, B x W uint64; flags_dev device, B uint16: each frame's
+ *              result, written by this call (stage-1 frames) or by the step in
+ *              which the frame finishes. They must stay valid until then.
+ *   done_dev   device, B int32, or NULL: for each frame, when it finished --
+ *              -(s + 1) for a frame that passed stage 1 in submission s (the
+ *              pool's submissions numbered from 0), or k >= 1 for a frame that
+ *              finished in the pool's k-th step.
+ * MPWSD_ENOMEM (nothing launched) when B exceeds mpwsd_pool_free_frames.
+ * Asynchronous on `stream`.
+ */
+MPWSD_API int mpwsd_pool_submit(mpwsd_pool *pool, const float *y_dev, int64_t B, uint64_t *cw_dev, uint16_t *flags_dev,
+                                int32_t *done_dev, void *stream);
+
+/*
+ * mpwsd_pool_step -- one iteration of Algorithm 1 on every row of the pool,
+ * then the final choice for the frames that finished in it (see above). A
+ * step with no rows launches the same kernels, which find nothing to do.
+ * Asynchronous on `stream`.
+ */
+MPWSD_API int mpwsd_pool_step(mpwsd_pool *pool, void *stream);
 
 /*
  * mpwsd_decode_noalloc -- mpwsd_decode for callers that cannot allocate device

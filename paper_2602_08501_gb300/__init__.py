@@ -3,6 +3,7 @@ Python binding. Build the shared library with ``paper_2602_08501_gb300.build``."
 from .mpwsd import (  # noqa: F401
     Code,
     MpwsdError,
+    Pool,
     Workspace,
     declared_symbols,
     enumerate_codewords,

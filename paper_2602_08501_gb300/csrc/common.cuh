@@ -108,6 +108,20 @@ __device__ __forceinline__ bool apply_decision(const Workspace &ws, const CodeDe
 
 enum RowOutcome { kRowNone = 0, kRowHop = 1, kRowStop = 2, kRowRescan = 3 };
 
+// Pool mode: trajectory t (slot t / L) has ended; the last one of its slot
+// puts the slot on the step's completed list.
+__device__ __forceinline__ void pool_end_traj(const Workspace &ws, int t, int L) {
+    const int slot = t / L;
+    if (atomicSub(ws.pool.live + slot, 1) == 1) ws.pool.completed[atomicAdd(ws.pool.ctr + kPoolCompleted, 1)] = slot;
+}
+
+// Pool mode: a failing frame of a submission takes a free slot (the host keeps
+// the frames in flight within the pool's capacity, so one is always free).
+__device__ __forceinline__ int pool_take_slot(const Workspace &ws) {
+    const int k = atomicAdd(ws.pool.ctr + kPoolPop, 1);
+    return ws.pool.free_ring[(unsigned)k % (unsigned)ws.pool.cap];
+}
+
 // Active lists: iteration `iter` scores the rows of act[0] (count counters[1 +
 // iter]); the rows that hop go to act[1] (count counters[kHoppedBase + iter]),
 // and the duplicate retirement moves the distinct ones back into act[0] for

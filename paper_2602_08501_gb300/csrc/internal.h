@@ -40,6 +40,25 @@ struct DevStats {
     unsigned long long error;  // nonzero after a bounded device wait gave up
 };
 
+// Continuous stage-2 batching: a pool of frame slots that many submissions
+// share. A failing frame of a submission takes a free slot; its L trajectories
+// join the rows every pool step scores, whichever submission they came from
+// and however many iterations they have done. A trajectory ends when it stops,
+// reaches T hops or is retired as a twin; when the last one of a slot ends, the
+// step's final pass writes the frame's result where the submission asked and
+// frees the slot. All pointers are null in a one-batch decode.
+struct PoolDev {
+    int cap = 0;                   // slots
+    int T = 0;                     // iterations (hops) per trajectory at most
+    int *ctr = nullptr;            // kPool* counters below
+    int *free_ring = nullptr;      // cap: free slot ids, popped at ctr[kPoolPop], pushed at ctr[kPoolPush]
+    int *live = nullptr;           // cap: trajectories of the slot still running
+    int *completed = nullptr;      // cap: slots whose last trajectory ended in this step
+    unsigned long long *dst = nullptr;  // cap x 3: addresses of the frame's codeword, flags and done entry
+    float *slot_y = nullptr;       // cap x n: the frame's y (read by the exact re-rank and the rescan)
+};
+constexpr int kPoolPop = 0, kPoolPush = 1, kPoolSteps = 2, kPoolCompleted = 3, kPoolFinished = 4;
+
 // Per-decode device scratch. All arrays are sized for (max_B, max_L).
 struct Workspace {
     int64_t max_B = 0;
@@ -62,6 +81,7 @@ struct Workspace {
     float *split_val = nullptr;   // kSplitItemsPerSm * num_sms items x 256 rows x K partial lists
     int *split_idx = nullptr;
     int *unit_done = nullptr;     // per 256-row unit: chunks finished in the current launch
+    PoolDev pool;                 // continuous batching (null: one-batch decode)
 };
 
 // Work items of the split: at most this many per SM (units x chunks < 4 x SMs).
@@ -110,6 +130,8 @@ struct SclArgs {
     // decode mode
     uint64_t *cw_out;
     uint16_t *flags_out;
+    int32_t *done_out;   // pool mode: done entry of frame f (nullable)
+    int submit_id;       // pool mode: frames that pass stage 1 get done = -(submit_id + 1)
     Workspace ws;
     // list mode
     uint64_t *list_cw;
@@ -129,6 +151,8 @@ struct OsdArgs {
     int write_yhl;
     uint64_t *cw_out;
     uint16_t *flags_out;
+    int32_t *done_out;   // as in SclArgs
+    int submit_id;
     Workspace ws;
     uint64_t *list_cw;
     int64_t *list_d;
@@ -181,5 +205,9 @@ cudaError_t launch_rescan(const CodeDev &c, const Workspace &ws, int iter, int L
 cudaError_t launch_dedup(const CodeDev &c, const Workspace &ws, int iter, int L, cudaStream_t s);
 cudaError_t launch_final(const CodeDev &c, const Workspace &ws, int L, int T, int64_t B, uint64_t *cw_out, uint16_t *flags_out,
                          cudaStream_t s);
+// pool mode: final select of the slots completed in this step, their release,
+// and the step's bookkeeping (rows of the next step, counters, statistics)
+cudaError_t launch_pool_final(const CodeDev &c, const Workspace &ws, int L, cudaStream_t s);
+cudaError_t launch_pool_end(const CodeDev &c, const Workspace &ws, cudaStream_t s);
 
 }  // namespace mpwsd

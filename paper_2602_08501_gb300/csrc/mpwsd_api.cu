@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <deque>
 #include <mutex>
 #include <string>
 #include <unordered_set>
@@ -568,7 +569,8 @@ struct HostIO {
 };
 
 static cudaError_t stage1_launch(mpwsd_code *code, Workspace &ws, const float *y_dev, int64_t f0, int64_t B, int L,
-                                 const mpwsd_opts &o, uint64_t *cw_dev, uint16_t *flags_dev, cudaStream_t s) {
+                                 const mpwsd_opts &o, uint64_t *cw_dev, uint16_t *flags_dev, cudaStream_t s,
+                                 int32_t *done_dev = nullptr, int submit_id = 0) {
     CodeDev &d = code->d;
     const int W = d.W;
     if (o.stage1 == MPWSD_STAGE1_OSD) {
@@ -585,6 +587,8 @@ static cudaError_t stage1_launch(mpwsd_code *code, Workspace &ws, const float *y
         oa.write_yhl = o.score_mode == MPWSD_SCORE_BF16X2;
         oa.cw_out = cw_dev + f0 * W;
         oa.flags_out = flags_dev + f0;
+        oa.done_out = done_dev ? done_dev + f0 : nullptr;
+        oa.submit_id = submit_id;
         oa.ws = ws;
         return timed_launch(code, MPWSD_KERNEL_OSD, s, [&] { return launch_osd(d, oa, s); });
     }
@@ -598,6 +602,8 @@ static cudaError_t stage1_launch(mpwsd_code *code, Workspace &ws, const float *y
     sa.use_crc = d.crc_len > 0 && !o.always_on;
     sa.cw_out = cw_dev + f0 * W;
     sa.flags_out = flags_dev + f0;
+    sa.done_out = done_dev ? done_dev + f0 : nullptr;
+    sa.submit_id = submit_id;
     sa.ws = ws;
     sa.write_yhl = o.score_mode == MPWSD_SCORE_BF16X2;
     return timed_launch(code, MPWSD_KERNEL_SCL, s, [&] { return launch_scl(d, sa, s); });
@@ -1149,4 +1155,237 @@ extern "C" int mpwsd_decode_noalloc(mpwsd_code *code, const float *y_dev, int64_
     cudaGetDevice(&ws.device);
     ws_layout(code->d, B, L, &ws);
     return decode_impl(code, ws, y_dev, B, L, T, o, cw_dev, flags_dev, (cudaStream_t)stream);
+}
+
+// ---- continuous stage-2 batching (pools) ---------------------------------------
+//
+// A pool keeps the stage-2 state of one code across calls. mpwsd_pool_submit
+// runs stage 1 on a batch; its CRC-failing frames take slots of the pool and
+// their trajectories join the rows of the next step. mpwsd_pool_step runs one
+// iteration of Algorithm 1 (score, exact re-rank, hop, twin retirement) on
+// every live row, whatever submission it came from, then writes the results of
+// the frames that finished and frees their slots. Every trajectory ends after
+// at most T steps, so a submission's frames are all done T steps after it: the
+// host bounds the frames in flight by the submissions of the last T steps and
+// needs no read-back.
+
+struct mpwsd_pool {
+    mpwsd_code *code = nullptr;
+    Workspace w;
+    int L = 0, T = 0;
+    mpwsd_opts o{};
+    int64_t cap = 0;
+    int64_t steps = 0, submits = 0, in_flight = 0;
+    std::deque<std::pair<int64_t, int64_t>> recent;  // (steps before the submission, frames)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_kernels = 0;
+};
+
+static int pool_step_launches(mpwsd_pool *p, cudaStream_t s) {
+    mpwsd_code *code = p->code;
+    CodeDev &d = code->d;
+    Workspace &ws = p->w;
+    ScoreArgs a{};
+    a.y = ws.pool.slot_y;
+    a.rows = ws.act[0];
+    a.n_rows_dev = ws.counters + 1;
+    a.cw = ws.traj_cw;
+    a.slot_frame = ws.slot_frame;
+    a.L = p->L;
+    a.topk_val = ws.topk_val;
+    a.topk_idx = ws.topk_idx;
+    a.yhl = ws.slot_yhl;
+    a.l1 = ws.slot_l1;
+    a.split_val = ws.split_val;
+    a.split_idx = ws.split_idx;
+    a.unit_done = ws.unit_done;
+    a.split_items = d.split_items;
+    cudaError_t e = launch_score(code, p->o.score_mode, a, s);
+    if (e != cudaSuccess) return cuda_fail(e, "scoring launch");
+    const float *y = ws.pool.slot_y;
+    const int L = p->L;
+    e = timed_launch(code, MPWSD_KERNEL_HOP, s, [&] { return launch_hop(d, ws, 0, L, y, s); });
+    if (e == cudaSuccess) e = timed_launch(code, MPWSD_KERNEL_RESCAN, s, [&] { return launch_rescan(d, ws, 0, L, y, s); });
+    if (e == cudaSuccess) e = timed_launch(code, MPWSD_KERNEL_HOP, s, [&] { return launch_dedup(d, ws, 0, L, s); });
+    if (e == cudaSuccess) e = timed_launch(code, MPWSD_KERNEL_FINAL, s, [&] { return launch_pool_final(d, ws, L, s); });
+    if (e == cudaSuccess) e = timed_launch(code, MPWSD_KERNEL_FINAL, s, [&] { return launch_pool_end(d, ws, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "pool step launch");
+    return MPWSD_OK;
+}
+
+// Device layout of a pool: the workspace arrays for (max_frames, L), the
+// buffers of the scoring kernel's pattern split, and the pool's own arrays.
+struct PoolLayout {
+    size_t sv, si, ud, ctr, ring, live, comp, dst, y, total;
+    size_t split_items;
+};
+static PoolLayout pool_layout(const CodeDev &d, int64_t max_frames, int L) {
+    PoolLayout l{};
+    size_t off = ws_layout(d, max_frames, L, nullptr);
+    auto take = [&](size_t bytes) {
+        size_t r = off;
+        off += align256(bytes);
+        return r;
+    };
+    l.split_items = (size_t)kSplitItemsPerSm * std::max(d.num_sms, 1);
+    const size_t split_entries = l.split_items * 256 * kTopK;
+    l.sv = take(split_entries * 4);
+    l.si = take(split_entries * 4);
+    l.ud = take(l.split_items * 4);
+    l.ctr = take(64 * 4);
+    l.ring = take((size_t)max_frames * 4);
+    l.live = take((size_t)max_frames * 4);
+    l.comp = take((size_t)max_frames * 4);
+    l.dst = take((size_t)max_frames * 3 * 8);
+    l.y = take((size_t)max_frames * d.n * 4);
+    l.total = off;
+    return l;
+}
+
+extern "C" int mpwsd_pool_bytes(const mpwsd_code *code, int64_t max_frames, int L, size_t *bytes) {
+    if (!code || !bytes) return fail(MPWSD_EINVAL, "NULL argument");
+    if (L < 1 || L > MPWSD_MAX_L) return fail(MPWSD_EINVAL, "L = %d: must be 1..%d", L, MPWSD_MAX_L);
+    if (max_frames < 1 || max_frames * L > 0x7fffffffLL)
+        return fail(MPWSD_EINVAL, "max_frames = %lld: need 1 <= max_frames and max_frames * L < 2^31", (long long)max_frames);
+    *bytes = pool_layout(code->d, max_frames, L).total;
+    return MPWSD_OK;
+}
+
+extern "C" int mpwsd_pool_create(mpwsd_code *code, int64_t max_frames, int L, int T, const mpwsd_opts *opts,
+                                 mpwsd_pool **out) {
+    if (!out) return fail(MPWSD_EINVAL, "out is NULL");
+    *out = nullptr;
+    mpwsd_opts o;
+    int st = check_decode_args(code, nullptr, 0, L, T, opts, nullptr, nullptr, &o);
+    if (st) return st;
+    if (max_frames < 1 || max_frames * L > 0x7fffffffLL)
+        return fail(MPWSD_EINVAL, "max_frames = %lld: need 1 <= max_frames and max_frames * L < 2^31", (long long)max_frames);
+    const CodeDev &d = code->d;
+    const PoolLayout lay = pool_layout(d, max_frames, L);
+    const size_t o_sv = lay.sv, o_si = lay.si, o_ud = lay.ud, o_ctr = lay.ctr, o_ring = lay.ring, o_live = lay.live;
+    const size_t o_comp = lay.comp, o_dst = lay.dst, o_y = lay.y, off = lay.total;
+    const size_t split_items = lay.split_items;
+    mpwsd_pool *p = new (std::nothrow) mpwsd_pool();
+    if (!p) return fail(MPWSD_ENOMEM, "host allocation");
+    p->code = code;
+    p->L = L;
+    p->T = T;
+    p->o = o;
+    p->cap = max_frames;
+    cudaError_t e = dev_alloc(&p->w.base, off);
+    if (e != cudaSuccess) {
+        delete p;
+        cudaGetLastError();
+        return cuda_fail(e, "pool allocation");
+    }
+    p->w.bytes = off;
+    p->w.max_B = max_frames;
+    p->w.max_L = L;
+    cudaGetDevice(&p->w.device);
+    ws_layout(d, max_frames, L, &p->w);
+    char *b = (char *)p->w.base;
+    p->w.split_val = (float *)(b + o_sv);
+    p->w.split_idx = (int *)(b + o_si);
+    p->w.unit_done = (int *)(b + o_ud);
+    PoolDev &pd = p->w.pool;
+    pd.cap = (int)max_frames;
+    pd.T = T;
+    pd.ctr = (int *)(b + o_ctr);
+    pd.free_ring = (int *)(b + o_ring);
+    pd.live = (int *)(b + o_live);
+    pd.completed = (int *)(b + o_comp);
+    pd.dst = (unsigned long long *)(b + o_dst);
+    pd.slot_y = (float *)(b + o_y);
+    // every slot free; no rows; counters at zero
+    std::vector<int> ring((size_t)max_frames);
+    for (int64_t i = 0; i < max_frames; ++i) ring[(size_t)i] = (int)i;
+    int ctr[64] = {0};
+    ctr[kPoolPush] = (int)max_frames;
+    e = cudaMemset(p->w.counters, 0, 64 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->w.unit_done, 0, split_items * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(pd.ctr, ctr, sizeof(ctr), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pd.free_ring, ring.data(), ring.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p->w.base);
+        delete p;
+        return cuda_fail(e, "pool initialisation");
+    }
+    *out = p;
+    return MPWSD_OK;
+}
+
+extern "C" void mpwsd_pool_free(mpwsd_pool *p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    cudaFree(p->w.base);
+    delete p;
+}
+
+extern "C" int mpwsd_pool_free_frames(const mpwsd_pool *p, int64_t *frames) {
+    if (!p || !frames) return fail(MPWSD_EINVAL, "NULL argument");
+    *frames = p->cap - p->in_flight;
+    return MPWSD_OK;
+}
+
+extern "C" int mpwsd_pool_submit(mpwsd_pool *p, const float *y_dev, int64_t B, uint64_t *cw_dev, uint16_t *flags_dev,
+                                 int32_t *done_dev, void *stream) {
+    if (!p) return fail(MPWSD_EINVAL, "pool is NULL");
+    if (B < 0) return fail(MPWSD_EINVAL, "B < 0");
+    if (B > 0 && (!y_dev || !cw_dev || !flags_dev)) return fail(MPWSD_EINVAL, "NULL buffer");
+    if (B > p->cap - p->in_flight)
+        return fail(MPWSD_ENOMEM, "pool full: %lld frames submitted, %lld free until earlier frames finish",
+                    (long long)B, (long long)(p->cap - p->in_flight));
+    if (B == 0) return MPWSD_OK;
+    cudaError_t e = stage1_launch(p->code, p->w, y_dev, 0, B, p->L, p->o, cw_dev, flags_dev, (cudaStream_t)stream,
+                                  done_dev, (int)p->submits);
+    if (e != cudaSuccess) return cuda_fail(e, "stage-1 launch");
+    p->submits++;
+    p->in_flight += B;
+    p->recent.emplace_back(p->steps, B);
+    return MPWSD_OK;
+}
+
+extern "C" int mpwsd_pool_step(mpwsd_pool *p, void *stream) {
+    if (!p) return fail(MPWSD_EINVAL, "pool is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    mpwsd_code *code = p->code;
+    int st = MPWSD_OK;
+    if (p->o.use_graph && !code->profiling) {
+        if (!p->graph) {
+            cudaError_t e = cudaSuccess;
+            if (!p->cap_stream) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed);
+            if (e != cudaSuccess) return cuda_fail(e, "capturing the pool step");
+            t_capturing = true;
+            st = pool_step_launches(p, p->cap_stream);
+            t_capturing = false;
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamEndCapture(p->cap_stream, &graph);
+            if (st) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&p->graph, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+            p->graph_kernels = 6;
+        }
+        cudaError_t e = cudaGraphLaunch(p->graph, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        code->launches += p->graph_kernels;
+    } else {
+        st = pool_step_launches(p, s);
+        if (st) return st;
+    }
+    p->steps++;
+    // a submission made before step k is done after step k + T - 1
+    while (!p->recent.empty() && p->recent.front().first + p->T <= p->steps) {
+        p->in_flight -= p->recent.front().second;
+        p->recent.pop_front();
+    }
+    return MPWSD_OK;
 }

@@ -154,6 +154,8 @@ __global__ void __launch_bounds__(kOsdWarps * 32, 8) osd_kernel(const OsdArgs a,
     uint32_t lm[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) lm[i] = 0u - (((uint32_t)lane >> i) & 1u);
+    if (a.ws.pool.cap > 0 && blockIdx.x == 0 && threadIdx.x == 0 && a.mode == 0)
+        atomicAdd(&c.stats->frames, (unsigned long long)a.B);  // pool: counted per submission
     for (int64_t f = (int64_t)blockIdx.x * kOsdWarps + warp; f < a.B; f += (int64_t)gridDim.x * kOsdWarps) {
         // ---- 1. hard decisions, reliabilities ----
         uint32_t key[EPL];
@@ -343,19 +345,33 @@ __global__ void __launch_bounds__(kOsdWarps * 32, 8) osd_kernel(const OsdArgs a,
 #pragma unroll
                 for (int x = 0; x < W; ++x) a.cw_out[f * W + x] = cw[x];
                 a.flags_out[f] = (uint16_t)MPWSD_FLAG_CRC_OK;
+                if (a.done_out) a.done_out[f] = -(a.submit_id + 1);
             }
             __syncwarp();
             continue;
         }
+        const bool pool = a.ws.pool.cap > 0;
         int slot = 0, base = 0;
         if (lane == 0) {
-            slot = atomicAdd(&a.ws.counters[0], 1);
+            slot = pool ? pool_take_slot(a.ws) : atomicAdd(&a.ws.counters[0], 1);
             base = atomicAdd(&a.ws.counters[1], count);
-            a.ws.slot_frame[slot] = (int)(a.f0 + f);
+            // a pool slot keeps its own copy of y, so y is read at the slot itself
+            a.ws.slot_frame[slot] = pool ? slot : (int)(a.f0 + f);
             a.ws.slot_l1[slot] = (float)asum * (1.0f / 524288.0f);
+            if (pool) {
+                a.ws.pool.live[slot] = count;
+                unsigned long long *d = a.ws.pool.dst + 3 * (int64_t)slot;
+                d[0] = (unsigned long long)(a.cw_out + f * W);
+                d[1] = (unsigned long long)(a.flags_out + f);
+                d[2] = a.done_out ? (unsigned long long)(a.done_out + f) : 0ull;
+            }
         }
         slot = __shfl_sync(kAll, slot, 0);
         base = __shfl_sync(kAll, base, 0);
+        if (pool)
+            for (int j = lane; j < N; j += 32)
+                a.ws.pool.slot_y[(int64_t)slot * N + j] =
+                    (bit_at<W>(hdw, j) ? -(float)sm.a[j] : (float)sm.a[j]) * (1.0f / 524288.0f);
         if (a.write_yhl) {
             // y in the split form the tensor-core scoring consumes (see the SC-list kernel)
             uint32_t *dst = a.ws.slot_yhl + (int64_t)slot * N;

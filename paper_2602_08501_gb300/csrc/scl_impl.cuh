@@ -21,7 +21,7 @@
 #include <math_constants.h>
 #include <stdint.h>
 
-#include "internal.h"
+#include "common.cuh"
 
 namespace mpwsd {
 namespace scl_detail {
@@ -327,6 +327,8 @@ __global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32) scl_kernel(const
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int seg = lane / LW, sl = lane % LW;
     const int64_t fbase = ((int64_t)blockIdx.x * WPB + warp) * FPW;
+    if (a.ws.pool.cap > 0 && blockIdx.x == 0 && threadIdx.x == 0 && a.mode == 0)
+        atomicAdd(&c.stats->frames, (unsigned long long)a.B);  // pool: counted per submission
     if (fbase >= a.B) return;  // whole warp leaves together
     for (int idx = lane; idx < FPW * N; idx += 32) {
         const int64_t f = fbase + idx / N;
@@ -395,19 +397,21 @@ __global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32) scl_kernel(const
     int key = (ok && (a.rule == MPWSD_RULE_ANY || pos == 0)) ? pos : 0x7fff;
 #pragma unroll
     for (int o = LW / 2; o >= 1; o >>= 1) key = min(key, __shfl_xor_sync(segmask, key, o, LW));
+    const bool pool = a.ws.pool.cap > 0;
     if (key != 0x7fff) {
         if (pos == key) {
             uint64_t *dst = a.cw_out + frame * W;
             dst[0] = cw[0];
             if (W > 1) dst[1] = cw[1];
             a.flags_out[frame] = (uint16_t)MPWSD_FLAG_CRC_OK;
+            if (a.done_out) a.done_out[frame] = -(a.submit_id + 1);
         }
         return;
     }
     // stage 2: this frame becomes a slot with one trajectory per list entry
     int slot = 0, base = 0;
     if (sl == 0) {
-        slot = atomicAdd(&a.ws.counters[0], 1);
+        slot = pool ? pool_take_slot(a.ws) : atomicAdd(&a.ws.counters[0], 1);
         base = atomicAdd(&a.ws.counters[1], count);
     }
     slot = __shfl_sync(segmask, slot, 0, LW);
@@ -415,9 +419,19 @@ __global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32) scl_kernel(const
     if (sl == 0) {
         int l1 = 0;
         for (int j = 0; j < N; ++j) l1 += abs(cx.ych[j]);
-        a.ws.slot_frame[slot] = (int)(a.f0 + frame);
+        // a pool slot keeps its own copy of y, so y is read at the slot itself
+        a.ws.slot_frame[slot] = pool ? slot : (int)(a.f0 + frame);
         a.ws.slot_l1[slot] = (float)l1 * (1.0f / 524288.0f);
+        if (pool) {
+            a.ws.pool.live[slot] = count;
+            unsigned long long *d = a.ws.pool.dst + 3 * (int64_t)slot;
+            d[0] = (unsigned long long)(a.cw_out + frame * W);
+            d[1] = (unsigned long long)(a.flags_out + frame);
+            d[2] = a.done_out ? (unsigned long long)(a.done_out + frame) : 0ull;
+        }
     }
+    if (pool)
+        for (int j = sl; j < N; j += LW) a.ws.pool.slot_y[(int64_t)slot * N + j] = (float)cx.ych[j] * (1.0f / 524288.0f);
     if (a.write_yhl) {
         // y in the split form the tensor-core scoring consumes: word w holds
         // elements 2w (low half) and 2w+1 of hi = bf16(y) and of lo = bf16(y - hi)

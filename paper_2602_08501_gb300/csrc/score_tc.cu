@@ -74,7 +74,7 @@ struct TcCfg {
     static constexpr int B_STAGES = 2;
     // A builders: one or two per row block (warps 2-3, then 12-13), each
     // filling BM / (BUILDERS / RB) rows of its row block per unit
-    static constexpr int BUILDERS = (N == 64) ? 4 : 2;
+    static constexpr int BUILDERS = 2;
     static constexpr int QN = BM / 32 / (BUILDERS / RB);   // 32-row slices per builder
     static constexpr int THREADS = (4 + kEpiWarps + BUILDERS - 2) * 32;
     static constexpr int A_PART_BYTES = BM * N * 2;      // one row block, hi or lo

@@ -96,6 +96,11 @@ __global__ void __launch_bounds__(kHopThreads) hop_kernel(const Workspace ws, co
                     outcome = kRowHop;
                     ++my_hops;
                 }
+                // pool: a trajectory ends when it stops or has made its T hops
+                if (ws.pool.cap > 0 && (outcome == kRowStop || (int)((st & kTrajHopsMask) + 1u) >= ws.pool.T)) {
+                    pool_end_traj(ws, t, L);
+                    outcome = kRowNone;
+                }
             }
         }
         route_row(ws, iter, outcome, t);
@@ -155,10 +160,12 @@ __global__ void __launch_bounds__(kHopThreads) rescan_kernel(const Workspace ws,
             }
             ws.traj_state[t] |= kTrajRescan;
             atomicAdd(&c.stats->rescans, 1ull);
-            if (apply_decision(ws, c, t, bp, best)) {
+            const bool hop = apply_decision(ws, c, t, bp, best);
+            if (hop) atomicAdd(&c.stats->hops, 1ull);
+            if (ws.pool.cap > 0 && (!hop || (int)(ws.traj_state[t] & kTrajHopsMask) >= ws.pool.T))
+                pool_end_traj(ws, t, L);  // pool: stopped, or its T hops are done
+            else if (hop)
                 act_out[atomicAdd(n_out, 1)] = t;
-                atomicAdd(&c.stats->hops, 1ull);
-            }
         }
         __syncthreads();
     }
@@ -213,7 +220,10 @@ __global__ void __launch_bounds__(kHopThreads) dedup_kernel(const Workspace ws, 
                     dup |= (st2[u] & kTrajValid) && !(st2[u] & kTrajRetired) && a2[u] == c0 && b2[u] == c1;
             }
             keep = !dup;
-            if (dup) ws.traj_state[t] |= kTrajRetired;
+            if (dup) {
+                ws.traj_state[t] |= kTrajRetired;
+                if (ws.pool.cap > 0) pool_end_traj(ws, t, L);
+            }
         }
         const int po = append_slot(0xffffffffu, n_out, keep);
         if (po >= 0) ws.act[0][po] = t;
@@ -266,7 +276,81 @@ __global__ void __launch_bounds__(kHopThreads) final_kernel(const Workspace ws, 
     }
 }
 
+// Pool mode: the frames whose last trajectory ended in this step. Same choice
+// as final_kernel (smallest ED, lowest anchor on ties); the result goes where
+// the frame's submission asked, with the step number as its done entry, and
+// the slot returns to the free ring.
+__global__ void __launch_bounds__(kHopThreads) pool_final_kernel(const Workspace ws, const CodeDev c, int L) {
+    const PoolDev &p = ws.pool;
+    const int F = p.ctr[kPoolCompleted];
+    const int step = p.ctr[kPoolSteps] + 1;
+    const int W = c.W;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F; i += gridDim.x * blockDim.x) {
+        const int s = p.completed[i];
+        double best = CUDART_INF;
+        int bk = 0;
+        unsigned maxh = 0, rescan = 0;
+        for (int l = 0; l < L; ++l) {
+            const int64_t t = (int64_t)s * L + l;
+            const uint32_t st = ws.traj_state[t];
+            if (!(st & kTrajValid)) continue;
+            const double D = ws.traj_D[t];
+            if (D < best) {
+                best = D;
+                bk = l;
+            }
+            maxh = max(maxh, st & kTrajHopsMask);
+            rescan |= st & kTrajRescan;
+        }
+        const uint64_t *cw = ws.traj_cw + ((int64_t)s * L + bk) * W;
+        unsigned syn = 0;
+        for (int b = 0; b < c.crc_len; ++b) {
+            int q = 0;
+            for (int w = 0; w < W; ++w) q += __popcll(cw[w] & c.crc_masks[b * W + w]);
+            syn |= (unsigned)(q & 1);
+        }
+        const unsigned iters = min((unsigned)p.T, maxh + 1u);
+        uint16_t fl = (uint16_t)(MPWSD_FLAG_STAGE2 | (iters << MPWSD_FLAG_ITERS_SHIFT));
+        if (c.crc_len > 0 && syn == 0) fl |= MPWSD_FLAG_CRC_OK;
+        if (rescan) fl |= MPWSD_FLAG_RESCAN;
+        if (c.stats->error) fl |= MPWSD_FLAG_ERROR;
+        const unsigned long long *d = p.dst + 3 * (int64_t)s;
+        uint64_t *cw_out = (uint64_t *)d[0];
+        for (int w = 0; w < W; ++w) cw_out[w] = cw[w];
+        *(uint16_t *)d[1] = fl;
+        if (d[2]) *(int32_t *)d[2] = step;
+        p.free_ring[(unsigned)atomicAdd(p.ctr + kPoolPush, 1) % (unsigned)p.cap] = s;
+    }
+}
+
+// Pool mode, end of a step: the rows that go on (written by the twin
+// retirement from 0) become the next step's rows, after which submissions
+// append theirs; statistics of the step; the step count.
+__global__ void pool_end_kernel(const Workspace ws, const CodeDev c) {
+    const PoolDev &p = ws.pool;
+    const int scored = ws.counters[1], done = p.ctr[kPoolCompleted];
+    atomicAdd(&c.stats->pattern_evals, (unsigned long long)scored * (unsigned long long)c.P);
+    atomicAdd(&c.stats->stage2_frames, (unsigned long long)done);
+    ws.counters[1] = ws.counters[2];
+    ws.counters[2] = 0;
+    ws.counters[32] = 0;
+    ws.counters[kHoppedBase] = 0;
+    p.ctr[kPoolCompleted] = 0;
+    p.ctr[kPoolFinished] += done;
+    p.ctr[kPoolSteps] += 1;
+}
+
 }  // namespace
+
+cudaError_t launch_pool_final(const CodeDev &c, const Workspace &ws, int L, cudaStream_t s) {
+    pool_final_kernel<<<c.num_sms, kHopThreads, 0, s>>>(ws, c, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pool_end(const CodeDev &c, const Workspace &ws, cudaStream_t s) {
+    pool_end_kernel<<<1, 1, 0, s>>>(ws, c);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_hop(const CodeDev &c, const Workspace &ws, int iter, int L, const float *y, cudaStream_t s) {
     hop_kernel<<<c.num_sms * 8, kHopThreads, 0, s>>>(ws, c, iter, L, y);

@@ -95,6 +95,12 @@ def lib():
             "mpwsd_tune_get": (i32, [P, i32, ctypes.POINTER(ctypes.c_int)]),
             "mpwsd_profile_begin": (i32, [P]),
             "mpwsd_profile_end": (i32, [P, ctypes.POINTER(_KTime)]),
+            "mpwsd_pool_create": (i32, [P, i64, i32, i32, P, ctypes.POINTER(P)]),
+            "mpwsd_pool_free": (None, [P]),
+            "mpwsd_pool_bytes": (i32, [P, i64, i32, ctypes.POINTER(ctypes.c_size_t)]),
+            "mpwsd_pool_free_frames": (i32, [P, ctypes.POINTER(ctypes.c_int64)]),
+            "mpwsd_pool_submit": (i32, [P, P, i64, P, P, P, P]),
+            "mpwsd_pool_step": (i32, [P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -314,6 +320,15 @@ class Code:
     def workspace(self, max_B: int, max_L: int) -> Workspace:
         return Workspace(self, max_B, max_L)
 
+    def pool_bytes(self, max_frames: int, L: int) -> int:
+        b = ctypes.c_size_t(0)
+        _check(lib().mpwsd_pool_bytes(self._h, int(max_frames), int(L), ctypes.byref(b)), "pool_bytes")
+        return int(b.value)
+
+    def pool(self, max_frames: int, L: int, T: int, score_mode="bf16x2", rule="top1", always_on=False,
+             use_graph: bool = True, osd_order: int | None = None) -> "Pool":
+        return Pool(self, max_frames, L, T, score_mode, rule, always_on, use_graph, osd_order)
+
     def workspace_bytes(self, max_B: int, max_L: int) -> int:
         b = ctypes.c_size_t(0)
         _check(lib().mpwsd_workspace_bytes(self._h, int(max_B), int(max_L), ctypes.byref(b)), "workspace_bytes")
@@ -347,3 +362,60 @@ class Code:
         arr = (_KTime * len(KERNEL_NAMES))()
         _check(lib().mpwsd_profile_end(self._h, arr), "profile_end")
         return {name: {"launches": int(arr[i].launches), "ms": float(arr[i].ms)} for i, name in enumerate(KERNEL_NAMES)}
+
+
+class Pool:
+    """A stage-2 pool of the library (mpwsd_pool_*): continuous batching of
+    stage 2 across submissions of one code."""
+
+    def __init__(self, code: Code, max_frames: int, L: int, T: int, score_mode="bf16x2", rule="top1",
+                 always_on=False, use_graph: bool = True, osd_order: int | None = None):
+        self.code = code
+        self.L, self.T, self.max_frames = int(L), int(T), int(max_frames)
+        o = Code._opts(score_mode, rule, always_on, use_graph, osd_order)
+        h = ctypes.c_void_p()
+        _check(lib().mpwsd_pool_create(code._h, self.max_frames, self.L, self.T, ctypes.byref(o), ctypes.byref(h)),
+               "pool_create")
+        self._h = h
+        self.submits = 0
+        self.steps = 0
+
+    def free_frames(self) -> int:
+        v = ctypes.c_int64(0)
+        _check(lib().mpwsd_pool_free_frames(self._h, ctypes.byref(v)), "pool_free_frames")
+        return int(v.value)
+
+    def submit(self, y, cw_out, flags_out, done_out=None, stream=None) -> int:
+        """Stage 1 on y (B x n float32 CUDA tensor); results land in cw_out /
+        flags_out (and done_out, int32) when each frame finishes. Returns the
+        submission number."""
+        import torch
+
+        B = int(y.shape[0])
+        if y.dim() != 2 or y.shape[1] != self.code.n:
+            raise ValueError(f"y must be B x {self.code.n}")
+        done = _dev(done_out, torch.int32, "done_out") if done_out is not None else None
+        _check(lib().mpwsd_pool_submit(self._h, _dev(y, torch.float32, "y"), B, _dev(cw_out, torch.int64, "cw_out"),
+                                       _dev(flags_out, torch.int16, "flags_out"), done, _stream_ptr(stream)),
+               "pool_submit")
+        sid = self.submits
+        if B > 0:
+            self.submits += 1
+        return sid
+
+    def step(self, stream=None) -> int:
+        """One iteration of Algorithm 1 on every row of the pool; returns the step number (from 1)."""
+        _check(lib().mpwsd_pool_step(self._h, _stream_ptr(stream)), "pool_step")
+        self.steps += 1
+        return self.steps
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mpwsd_pool_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

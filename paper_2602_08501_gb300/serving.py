@@ -2,30 +2,33 @@
 
 Frames arrive over time, each for one of several codes. The loop:
 
-* admits work by device memory: every code owns a few *slots* (a decoder
-  workspace, device buffers for y / codewords / flags, a CUDA stream), created
-  up front while the memory budget allows -- a slot that does not fit
-  (over budget, or MPWSD_ENOMEM) is not created, so frames wait instead;
-* batches as work accrues: whenever a code has pending frames and a free slot,
-  it dispatches up to ``max_batch`` of them -- as soon as ``min_batch`` have
-  accrued or the oldest has waited ``max_wait_s`` -- so frames that arrive while
-  others are on the GPU are admitted as slots free up and their decodes overlap
-  on the device (one stream per slot). Each dispatch runs the whole two-stage
-  decode, whose stage 2 gathers the CRC-failing frames of the batch;
-* keeps decoder state on the GPU: inputs come straight from pinned host memory
-  into the slot's device buffer, the decode leaves results on the device and
-  one copy brings them back; batches are padded to size buckets so that the
-  decode's CUDA graph is replayed;
-* reports per-frame latency (completion, from CUDA events, minus arrival) and
-  throughput.
+* admits work by device memory: every code owns one stage-2 pool
+  (``mpwsd_pool_*``) whose slot count -- the frames it can hold in flight --
+  is what the device-memory budget allows; a code whose smallest pool does not
+  fit gets none (its frames are refused). Frames wait on the host while the
+  pool is full and enter as earlier frames finish;
+* batches stage-2 work as it accrues: arrived frames of a code are submitted
+  (stage 1 runs on them at once) as soon as ``min_batch`` have accrued or the
+  oldest has waited ``max_wait_s``; their CRC-failing frames join the pool, and
+  every pool step runs one iteration of Algorithm 1 on all rows of the pool --
+  trajectories of frames from many submissions, at different iterations --
+  so the scoring launches grow with the load instead of with one submission;
+* keeps decoder state on the GPU: y goes from pinned host memory into a
+  device staging buffer, each frame's result is written on the device where
+  the loop asked, and one copy brings all of them back at the end; each
+  code's pool runs on its own stream, so the codes' work overlaps on the
+  device, and the pool step is replayed from a CUDA graph;
+* reports per-frame latency (the CUDA event of the submission or step that
+  finished the frame, minus its arrival), throughput and the mean stage-2
+  rows per pool step.
 
-Padding frames are all-zero observations; frames are decoded independently,
-so a frame's result does not depend on what it was batched with.
+Frames are decoded independently, so a frame's result does not depend on what
+it was batched with (the tests check it against a one-batch decode and against
+decoding the frame alone).
 """
 from __future__ import annotations
 
 import time
-from collections import deque
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -41,35 +44,27 @@ class CodeSpec:
 
 
 @dataclass
-class _Slot:
-    name: str
-    ws: "mpwsd.Workspace"
-    y: object
-    cw: object
-    fl: object
-    stream: object
-    done: object
-    busy: bool = False
-    lo: int = 0
-    hi: int = 0
-    t_dispatch: float = 0.0
-
-
-@dataclass
 class ServeResult:
     latency_s: dict            # code -> per-frame latency (s), arrival order of that code
     cw: dict                   # code -> B x W uint64 codewords
     flags: dict                # code -> B uint16 flags
     served: int
     wall_s: float
-    dispatches: int
-    slots: dict                # code -> slots admitted
-    refused_slots: dict        # code -> slots refused by the memory budget
+    dispatches: int            # submissions
+    slots: dict                # code -> frames its pool holds in flight
+    refused_slots: dict        # code -> 1 if the budget fit no pool for it
     batch_sizes: list = field(default_factory=list)
+    steps: dict = field(default_factory=dict)           # code -> pool steps
+    stage2_rows: dict = field(default_factory=dict)     # code -> trajectory rows scored over all steps
+    submissions: dict = field(default_factory=dict)     # code -> submissions
 
     def percentiles(self, qs=(50, 99)):
         lat = np.concatenate([v for v in self.latency_s.values() if v.size]) if self.latency_s else np.zeros(0)
         return {f"p{q}": float(np.percentile(lat, q)) if lat.size else None for q in qs}
+
+    def rows_per_step(self):
+        steps = sum(self.steps.values())
+        return sum(self.stage2_rows.values()) / steps if steps else 0.0
 
 
 def _bucket(b: int, lo: int = 256) -> int:
@@ -79,10 +74,21 @@ def _bucket(b: int, lo: int = 256) -> int:
     return n
 
 
+def pool_frames_for_budget(code, L: int, want: int, budget: int | None, floor: int) -> int:
+    """The largest pool size <= want (halving from it) whose device memory fits
+    the budget, or 0 when not even `floor` frames fit."""
+    f = int(want)
+    while f >= floor:
+        if budget is None or code.pool_bytes(f, L) <= budget:
+            return f
+        f //= 2
+    return 0
+
+
 class Server:
-    def __init__(self, specs: dict, max_batch: int = 65536, slots_per_code: int = 4,
+    def __init__(self, specs: dict, max_batch: int = 65536, pool_frames: int | None = None,
                  mem_budget_bytes: int | None = None, min_batch: int = 4096, max_wait_s: float = 200e-6,
-                 score_mode: str = "bf16x2", use_graph: bool = True):
+                 score_mode: str = "bf16x2", use_graph: bool = True, steps_ahead: int = 2):
         import torch
 
         self.torch = torch
@@ -90,58 +96,49 @@ class Server:
         self.max_batch = int(max_batch)
         self.min_batch = int(min_batch)
         self.max_wait_s = float(max_wait_s)
-        self.score_mode = score_mode
-        self.use_graph = use_graph
-        self.slots: dict[str, list[_Slot]] = {}
-        self.refused: dict[str, int] = {}
-        budget = mem_budget_bytes
-        used = 0
-        per_slot = {}
+        self.steps_ahead = int(steps_ahead)
+        want = int(pool_frames) if pool_frames else 4 * self.max_batch
+        share = None if mem_budget_bytes is None else int(mem_budget_bytes) // max(1, len(specs))
+        self.pools, self.refused, self.streams, self.y_stage = {}, {}, {}, {}
+        self.mem_used = 0
         for name, sp in specs.items():
-            self.slots[name] = []
+            # the staging buffer for y counts against the budget too
+            stage = self.max_batch * sp.code.n * 4
+            frames = pool_frames_for_budget(sp.code, sp.L, want, None if share is None else share - stage,
+                                            floor=min(256, want))
+            if frames == 0:
+                self.refused[name] = 1
+                continue
+            try:
+                self.pools[name] = sp.code.pool(frames, sp.L, sp.T, score_mode=score_mode, use_graph=use_graph)
+            except mpwsd.MpwsdError as e:
+                if e.status != mpwsd.ENOMEM:
+                    raise
+                self.refused[name] = 1
+                continue
             self.refused[name] = 0
-            per_slot[name] = sp.code.workspace_bytes(self.max_batch, sp.L) + \
-                self.max_batch * (sp.code.n * 4 + sp.code.W * 8 + 2)
-        # round-robin over the codes, so every code gets a slot before any gets a second
-        for _ in range(slots_per_code):
-            for name, sp in specs.items():
-                n, W = sp.code.n, sp.code.W
-                if budget is not None and used + per_slot[name] > budget:
-                    self.refused[name] += 1
-                    continue
-                try:
-                    ws = sp.code.workspace(self.max_batch, sp.L)
-                except mpwsd.MpwsdError as e:
-                    if e.status != mpwsd.ENOMEM:
-                        raise
-                    self.refused[name] += 1
-                    continue
-                used += per_slot[name]
-                self.slots[name].append(_Slot(
-                    name=name, ws=ws,
-                    y=torch.zeros((self.max_batch, n), dtype=torch.float32, device="cuda"),
-                    cw=torch.empty((self.max_batch, W), dtype=torch.int64, device="cuda"),
-                    fl=torch.empty((self.max_batch,), dtype=torch.int16, device="cuda"),
-                    stream=torch.cuda.Stream(), done=torch.cuda.Event(enable_timing=True)))
-        self.mem_used = used
+            self.mem_used += sp.code.pool_bytes(frames, sp.L) + stage
+            self.streams[name] = torch.cuda.Stream()
+            self.y_stage[name] = torch.zeros((self.max_batch, sp.code.n), dtype=torch.float32, device="cuda")
+
+    @property
+    def slots(self):
+        return {nm: p.max_frames for nm, p in self.pools.items()}
 
     def warmup(self):
-        """Record the decode graph of every batch bucket on every slot (all-zero
-        frames), so no capture happens while requests are being served."""
+        """Record every pool's step graph and run one submission through each
+        (all-zero frames), so nothing is captured while requests are served."""
         torch = self.torch
-        for nm, slots in self.slots.items():
+        for nm, pool in self.pools.items():
             sp = self.specs[nm]
-            for s in slots:
-                b = 256
-                while True:
-                    bp = min(b, self.max_batch)
-                    with torch.cuda.stream(s.stream):
-                        s.y[:bp].zero_()
-                        sp.code.decode(s.y[:bp], sp.L, sp.T, score_mode=self.score_mode, cw_out=s.cw[:bp],
-                                       flags_out=s.fl[:bp], stream=s.stream, workspace=s.ws, use_graph=self.use_graph)
-                    if bp >= self.max_batch:
-                        break
-                    b *= 2
+            b = min(256, self.max_batch)
+            cw = torch.empty((b, sp.code.W), dtype=torch.int64, device="cuda")
+            fl = torch.empty((b,), dtype=torch.int16, device="cuda")
+            with torch.cuda.stream(self.streams[nm]):
+                self.y_stage[nm][:b].zero_()
+                pool.submit(self.y_stage[nm][:b], cw, fl, stream=self.streams[nm])
+                for _ in range(sp.T):
+                    pool.step(stream=self.streams[nm])
         torch.cuda.synchronize()
 
     def run(self, arrivals: dict, y_pinned: dict) -> ServeResult:
@@ -150,77 +147,92 @@ class Server:
         torch = self.torch
         names = list(self.specs)
         for nm in names:
-            if len(arrivals[nm]) and not self.slots[nm]:
-                raise RuntimeError(f"no decoder slot fits the memory budget for code {nm}")
-        pending = {nm: deque() for nm in names}      # (lo, hi) ranges of arrived, undispatched frames
-        nxt = {nm: 0 for nm in names}                # next frame index not yet arrived
+            if len(arrivals[nm]) and nm not in self.pools:
+                raise RuntimeError(f"no stage-2 pool fits the memory budget for code {nm}")
         total = {nm: len(arrivals[nm]) for nm in names}
-        cw_out = {nm: torch.empty((total[nm], self.specs[nm].code.W), dtype=torch.int64).pin_memory() for nm in names}
-        fl_out = {nm: torch.empty((total[nm],), dtype=torch.int16).pin_memory() for nm in names}
-        done_t = {nm: np.full(total[nm], np.nan) for nm in names}
-        disp_queue = {nm: 0 for nm in names}          # frames dispatched so far (FIFO)
-        busy = []
-        dispatches = 0
+        dev = {nm: dict(cw=torch.empty((total[nm], self.specs[nm].code.W), dtype=torch.int64, device="cuda"),
+                        fl=torch.empty((total[nm],), dtype=torch.int16, device="cuda"),
+                        done=torch.zeros((total[nm],), dtype=torch.int32, device="cuda")) for nm in names}
+        nxt = {nm: 0 for nm in names}        # frames arrived so far
+        sub = {nm: 0 for nm in names}        # frames submitted so far
+        sub_ev = {nm: [] for nm in names}    # event after each submission
+        step_ev = {nm: [] for nm in names}   # event after each step
+        sub0 = {nm: self.pools[nm].submits if nm in self.pools else 0 for nm in names}
+        step0 = {nm: self.pools[nm].steps if nm in self.pools else 0 for nm in names}
+        last_sub_step = {nm: -10 ** 9 for nm in names}  # pool step count at the latest submission
         batch_sizes = []
+        for nm in names:
+            self.specs[nm].code.reset_stats()
         ref = torch.cuda.Event(enable_timing=True)
         ref.record(torch.cuda.current_stream())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        remaining = sum(total.values())
-        while remaining > 0:
+
+        def busy(nm):
+            pool = self.pools[nm]
+            return pool.steps - last_sub_step[nm] < pool.T
+
+        while any(sub[nm] < total[nm] or (nm in self.pools and busy(nm)) for nm in names):
             now = time.perf_counter() - t0
-            for nm in names:  # arrivals up to now
-                arr = arrivals[nm]
-                j = nxt[nm]
-                k = int(np.searchsorted(arr, now, side="right"))
-                if k > j:
-                    nxt[nm] = k
-            for s in list(busy):  # completions
-                if s.done.query():
-                    t_done = ref.elapsed_time(s.done) / 1e3
-                    done_t[s.name][s.lo:s.hi] = t_done
-                    remaining -= s.hi - s.lo
-                    s.busy = False
-                    busy.remove(s)
-            for nm in names:  # dispatch
-                avail = nxt[nm] - disp_queue[nm]
-                if avail <= 0:
+            for nm in names:
+                if nm not in self.pools:
                     continue
-                oldest = arrivals[nm][disp_queue[nm]]
-                if avail < self.min_batch and now - oldest < self.max_wait_s and nxt[nm] < total[nm]:
-                    continue
-                free = [s for s in self.slots[nm] if not s.busy]
-                if not free:
-                    continue
-                s = free[0]
-                lo = disp_queue[nm]
-                hi = min(lo + self.max_batch, nxt[nm])
-                b = hi - lo
-                bp = min(_bucket(b), self.max_batch)
-                sp = self.specs[nm]
-                with torch.cuda.stream(s.stream):
-                    s.y[:b].copy_(y_pinned[nm][lo:hi], non_blocking=True)
-                    if bp > b:
-                        s.y[b:bp].zero_()
-                    sp.code.decode(s.y[:bp], sp.L, sp.T, score_mode=self.score_mode, cw_out=s.cw[:bp],
-                                   flags_out=s.fl[:bp], stream=s.stream, workspace=s.ws, use_graph=self.use_graph)
-                    cw_out[nm][lo:hi].copy_(s.cw[:b], non_blocking=True)
-                    fl_out[nm][lo:hi].copy_(s.fl[:b], non_blocking=True)
-                    s.done.record(s.stream)
-                s.busy, s.lo, s.hi = True, lo, hi
-                busy.append(s)
-                disp_queue[nm] = hi
-                dispatches += 1
-                batch_sizes.append(b)
+                pool, st, sp = self.pools[nm], self.streams[nm], self.specs[nm]
+                nxt[nm] = int(np.searchsorted(arrivals[nm], now, side="right"))
+                pend = nxt[nm] - sub[nm]
+                if pend > 0:
+                    oldest = arrivals[nm][sub[nm]]
+                    due = pend >= self.min_batch or now - oldest >= self.max_wait_s or nxt[nm] == total[nm]
+                    b = min(pend, self.max_batch, pool.free_frames()) if due else 0
+                    if b > 0:
+                        lo, hi = sub[nm], sub[nm] + b
+                        with torch.cuda.stream(st):
+                            self.y_stage[nm][:b].copy_(y_pinned[nm][lo:hi], non_blocking=True)
+                            pool.submit(self.y_stage[nm][:b], dev[nm]["cw"][lo:hi], dev[nm]["fl"][lo:hi],
+                                        dev[nm]["done"][lo:hi], stream=st)
+                            ev = torch.cuda.Event(enable_timing=True)
+                            ev.record(st)
+                        sub_ev[nm].append(ev)
+                        sub[nm] = hi
+                        last_sub_step[nm] = pool.steps
+                        batch_sizes.append(b)
+                if busy(nm):
+                    # keep at most `steps_ahead` steps queued on the device
+                    evs = step_ev[nm]
+                    if len(evs) >= self.steps_ahead and not evs[-self.steps_ahead].query():
+                        continue
+                    with torch.cuda.stream(st):
+                        pool.step(stream=st)
+                        ev = torch.cuda.Event(enable_timing=True)
+                        ev.record(st)
+                    evs.append(ev)
         torch.cuda.synchronize()
-        first = min(arrivals[nm][0] for nm in names if total[nm])
-        last = max(np.nanmax(done_t[nm]) for nm in names if total[nm])
-        lat = {nm: done_t[nm] - arrivals[nm] for nm in names}
-        return ServeResult(latency_s=lat, cw={nm: cw_out[nm].numpy().view(np.uint64) for nm in names},
-                           flags={nm: fl_out[nm].numpy().view(np.uint16) for nm in names},
-                           served=sum(total.values()), wall_s=last - first, dispatches=dispatches,
-                           slots={nm: len(v) for nm, v in self.slots.items()}, refused_slots=dict(self.refused),
-                           batch_sizes=batch_sizes)
+        lat, cws, fls = {}, {}, {}
+        steps, rows = {}, {}
+        first = min((arrivals[nm][0] for nm in names if total[nm]), default=0.0)
+        last = first
+        for nm in names:
+            if not total[nm]:
+                lat[nm], cws[nm], fls[nm] = np.zeros(0), np.zeros((0, self.specs[nm].code.W), np.uint64), \
+                    np.zeros(0, np.uint16)
+                continue
+            done = dev[nm]["done"].cpu().numpy()
+            t_sub = np.array([ref.elapsed_time(e) / 1e3 for e in sub_ev[nm]])
+            t_step = np.array([ref.elapsed_time(e) / 1e3 for e in step_ev[nm]])
+            # done entries count the pool's submissions and steps from its creation
+            t_done = np.where(done < 0, t_sub[np.clip(-done - 1 - sub0[nm], 0, max(len(t_sub) - 1, 0))],
+                              t_step[np.clip(done - 1 - step0[nm], 0, max(len(t_step) - 1, 0))])
+            lat[nm] = t_done - arrivals[nm]
+            last = max(last, float(t_done.max()))
+            cws[nm] = dev[nm]["cw"].cpu().numpy().view(np.uint64)
+            fls[nm] = dev[nm]["fl"].cpu().numpy().view(np.uint16)
+            sp = self.specs[nm]
+            steps[nm] = self.pools[nm].steps - step0[nm]
+            rows[nm] = sp.code.stats()["pattern_evals"] // max(sp.code.n_patterns, 1)
+        return ServeResult(latency_s=lat, cw=cws, flags=fls, served=sum(total.values()), wall_s=last - first,
+                           dispatches=len(batch_sizes), slots=self.slots, refused_slots=dict(self.refused),
+                           batch_sizes=batch_sizes, steps=steps, stage2_rows=rows,
+                           submissions={nm: len(sub_ev[nm]) for nm in names})
 
 
 def poisson_arrivals(rate_hz: float, count: int, seed: int) -> np.ndarray:

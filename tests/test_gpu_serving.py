@@ -1,7 +1,8 @@
 """The continuous-batching request loop (serving.py) on a mixed two-code
 Poisson stream: every frame is served, each result is the same as when the
-frame is decoded in one big batch and when it is decoded alone, and a memory
-budget that cannot hold every slot refuses the extra slots but still serves."""
+frame is decoded in one big batch and when it is decoded alone, stage-2 rows
+from several submissions share the pool steps, and the memory budget sizes the
+pools (a budget that fits no pool for a code refuses that code)."""
 import numpy as np
 import pytest
 
@@ -26,7 +27,8 @@ def _setup(mp, n_each, rate, seed):
 def test_serving_results_equal_alone_and_in_one_batch():
     mp = cuda_or_skip()
     serving, specs, wls, arrivals, ys = _setup(mp, 6000, 2e6, seed=50)
-    srv = serving.Server(specs, max_batch=4096, slots_per_code=2, min_batch=512, max_wait_s=100e-6)
+    srv = serving.Server(specs, max_batch=4096, pool_frames=8192, min_batch=512, max_wait_s=100e-6)
+    srv.warmup()
     res = srv.run(arrivals, ys)
     assert res.served == 12000 and res.dispatches >= 4
     for nm, sp in specs.items():
@@ -41,6 +43,9 @@ def test_serving_results_equal_alone_and_in_one_batch():
             c1, f1 = sp.code.decode(torch.from_numpy(y[f:f + 1]).cuda(), sp.L, sp.T)
             torch.cuda.synchronize()
             assert np.array_equal(res.cw[nm][f], to_words(c1)[0]) and res.flags[nm][f] == f1.cpu().numpy().view(np.uint16)[0]
+        # frames of several submissions share a step: fewer steps than one stage 2 per submission would launch
+        assert 0 < res.steps[nm] and res.stage2_rows[nm] > 0
+    assert res.steps["rm26"] + res.steps["rm27"] < res.dispatches * 5
     p = res.percentiles()
     assert p["p50"] <= p["p99"] < 1.0
 
@@ -48,17 +53,23 @@ def test_serving_results_equal_alone_and_in_one_batch():
 def test_serving_admission_by_memory():
     mp = cuda_or_skip()
     serving, specs, wls, arrivals, ys = _setup(mp, 3000, 1e6, seed=60)
-    # room for about one slot per code
-    one = {nm: sp.code.workspace_bytes(2048, sp.L) + 2048 * (sp.code.n * 4 + sp.code.W * 8 + 2) for nm, sp in specs.items()}
-    srv = serving.Server(specs, max_batch=2048, slots_per_code=3, mem_budget_bytes=sum(one.values()) + 1024,
-                         min_batch=256, max_wait_s=100e-6)
-    assert {nm: len(v) for nm, v in srv.slots.items()} == {"rm26": 1, "rm27": 1} and sum(srv.refused.values()) == 4
+    stage = {nm: 2048 * sp.code.n * 4 for nm, sp in specs.items()}
+    # room for pools of about 1024 frames per code, not the 4096 asked for
+    budget = 2 * max(sp.code.pool_bytes(1024, sp.L) + stage[nm] for nm, sp in specs.items()) + 1024
+    srv = serving.Server(specs, max_batch=2048, pool_frames=4096, mem_budget_bytes=budget, min_batch=256,
+                         max_wait_s=100e-6)
+    assert all(256 <= v < 4096 for v in srv.slots.values()) and sum(srv.refused.values()) == 0
     res = srv.run(arrivals, ys)
-    assert res.served == 6000 and sum(res.refused_slots.values()) > 0
+    assert res.served == 6000
     for nm, sp in specs.items():
         cw, fl = sp.code.decode(torch.from_numpy(wls[nm].y).cuda(), sp.L, sp.T)
         torch.cuda.synchronize()
         assert np.array_equal(res.cw[nm], to_words(cw))
+    # a budget that holds no pool refuses the code
+    tiny = serving.Server(specs, max_batch=2048, pool_frames=4096, mem_budget_bytes=1 << 20)
+    assert tiny.refused == {"rm26": 1, "rm27": 1}
+    with pytest.raises(RuntimeError):
+        tiny.run(arrivals, ys)
 
 
 def test_autotune_picks_a_candidate_and_output_is_unchanged(tmp_path, monkeypatch):

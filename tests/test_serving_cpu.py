@@ -39,3 +39,24 @@ def test_latency_percentiles_pool_every_code():
     empty = serving.ServeResult(latency_s={}, cw={}, flags={}, served=0, wall_s=0.0, dispatches=0, slots={},
                                 refused_slots={})
     assert empty.percentiles() == {"p50": None, "p99": None}
+
+
+def test_pool_size_for_budget_halves_until_it_fits():
+    class FakeCode:
+        def pool_bytes(self, frames, L):
+            return 1000 + frames * L * 10
+
+    c = FakeCode()
+    assert serving.pool_frames_for_budget(c, 8, 4096, None, 256) == 4096
+    assert serving.pool_frames_for_budget(c, 8, 4096, 1000 + 4096 * 80, 256) == 4096
+    assert serving.pool_frames_for_budget(c, 8, 4096, 1000 + 4095 * 80, 256) == 2048
+    assert serving.pool_frames_for_budget(c, 8, 4096, 1000 + 300 * 80, 256) == 256
+    assert serving.pool_frames_for_budget(c, 8, 4096, 1000 + 255 * 80, 256) == 0
+
+
+def test_rows_per_step_pools_every_code():
+    res = serving.ServeResult(latency_s={}, cw={}, flags={}, served=0, wall_s=1.0, dispatches=3, slots={},
+                              refused_slots={}, steps={"a": 10, "b": 30}, stage2_rows={"a": 1000, "b": 3000})
+    assert res.rows_per_step() == 100.0
+    assert serving.ServeResult(latency_s={}, cw={}, flags={}, served=0, wall_s=1.0, dispatches=0, slots={},
+                               refused_slots={}).rows_per_step() == 0.0
