@@ -644,7 +644,8 @@ def run_serving(args):
              "rm27": synth.make_workload("rm27_crc6", (0.5, 3.0), n_max, seed=5)}
     ys = {nm: torch.from_numpy(pools[nm].y).pin_memory() for nm in specs}
     srv = serving.Server(specs, max_batch=args.serve_batch, pool_frames=4 * args.serve_batch,
-                         min_batch=args.serve_batch // 8, max_wait_s=args.serve_wait_us * 1e-6)
+                         min_batch=args.serve_batch // 8, max_wait_s=args.serve_wait_us * 1e-6,
+                         pools_per_code=args.serve_pools)
     srv.warmup()  # records each pool's step graph
     out = []
     for rate in rates:
@@ -665,7 +666,7 @@ def run_serving(args):
             "n_gpus": 1, "higher_is_better": True, "dtype": "bf16x2+f64", "data": "synthetic",
             "config": {"workload": "serving: Poisson arrivals, 50/50 RM(2,6)+CRC-6 (L=8,T=4) / RM(2,7)+CRC-6 (L=16,T=6), "
                                    "Eb/N0 U[0.5,3] dB; one stage-2 pool per code (continuous batching)",
-                       "max_batch": args.serve_batch, "pool_frames": srv.slots,
+                       "max_batch": args.serve_batch, "pool_frames": srv.slots, "pools_per_code": args.serve_pools,
                        "max_wait_us": args.serve_wait_us, "seconds_per_rate": args.serve_seconds},
             "rates": out}
     print(json.dumps(line), flush=True)
@@ -690,6 +691,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=0.1, help="serving: seconds of traffic per rate")
     ap.add_argument("--serve-batch", type=int, default=65536)
     ap.add_argument("--serve-wait-us", type=float, default=200.0)
+    ap.add_argument("--serve-pools", type=int, default=1, help="serving: stage-2 pools per code (one stream each)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     if args.workload == "serving":

@@ -54,11 +54,11 @@ def test_serving_admission_by_memory():
     mp = cuda_or_skip()
     serving, specs, wls, arrivals, ys = _setup(mp, 3000, 1e6, seed=60)
     stage = {nm: 2048 * sp.code.n * 4 for nm, sp in specs.items()}
-    # room for pools of about 1024 frames per code, not the 4096 asked for
-    budget = 2 * max(sp.code.pool_bytes(1024, sp.L) + stage[nm] for nm, sp in specs.items()) + 1024
+    # room for pools of about 1024 frames (two per code), not the 4096 asked for
+    budget = 4 * max(sp.code.pool_bytes(1024, sp.L) + stage[nm] for nm, sp in specs.items()) + 1024
     srv = serving.Server(specs, max_batch=2048, pool_frames=4096, mem_budget_bytes=budget, min_batch=256,
-                         max_wait_s=100e-6)
-    assert all(256 <= v < 4096 for v in srv.slots.values()) and sum(srv.refused.values()) == 0
+                         max_wait_s=100e-6, pools_per_code=2)
+    assert all(2 * 256 <= v < 2 * 4096 for v in srv.slots.values()) and sum(srv.refused.values()) == 0
     res = srv.run(arrivals, ys)
     assert res.served == 6000
     for nm, sp in specs.items():
@@ -66,8 +66,8 @@ def test_serving_admission_by_memory():
         torch.cuda.synchronize()
         assert np.array_equal(res.cw[nm], to_words(cw))
     # a budget that holds no pool refuses the code
-    tiny = serving.Server(specs, max_batch=2048, pool_frames=4096, mem_budget_bytes=1 << 20)
-    assert tiny.refused == {"rm26": 1, "rm27": 1}
+    tiny = serving.Server(specs, max_batch=2048, pool_frames=4096, mem_budget_bytes=1 << 20, pools_per_code=2)
+    assert tiny.refused == {"rm26": 2, "rm27": 2}
     with pytest.raises(RuntimeError):
         tiny.run(arrivals, ys)
 
