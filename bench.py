@@ -420,6 +420,17 @@ def run_ours(args, wl_cfg):
     fl_dev = torch.empty((frames,), dtype=torch.int16, device="cuda")
     stream = torch.cuda.current_stream()
 
+    tuning = None
+    if args.tune:
+        # the autotuner times every scoring shape and split target on this batch
+        # (graph replays), applies the fastest and reports it beside the default
+        from paper_2602_08501_gb300 import autotune
+
+        if osd is None and not aom:
+            r = autotune.tune(code, y_dev, L, T, batch_sizes=(frames,), use_cache=False, reps=3)
+            tuning = {"shape": r["shape"], "split_items": r["value"], "default_ms": r["default_ms"],
+                      "tuned_ms": r["times_ms"][f"{r['shape']}/{r['value']}"], "times_ms": r["times_ms"]}
+
     def step():
         code.decode(y_dev, L, T, score_mode=args.mode, cw_out=cw_dev, flags_out=fl_dev, osd_order=osd,
                     always_on=aom)
@@ -594,6 +605,8 @@ def run_ours(args, wl_cfg):
         "gpu_launches": int(stats["kernel_launches"]),
         "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "sm_mhz_min", "reasons", "samples", "source")},
         "stats": {k: stats[k] for k in ("stage2_frames", "trajectories", "hops", "rerank_candidates", "rescans")},
+        "tuning": tuning if tuning else {"shape": code.tune_get(mpwsd.TUNE_TC_SHAPE),
+                                         "split_items": code.tune_get(mpwsd.TUNE_SPLIT_ITEMS), "tuned": False},
     }
 
     if rank == 0 and not args.no_cpu:
@@ -643,6 +656,13 @@ def run_serving(args):
     pools = {"rm26": synth.make_workload("rm26_crc6", (0.5, 3.0), n_max, seed=4),
              "rm27": synth.make_workload("rm27_crc6", (0.5, 3.0), n_max, seed=5)}
     ys = {nm: torch.from_numpy(pools[nm].y).pin_memory() for nm in specs}
+    from paper_2602_08501_gb300 import autotune
+
+    tuned = {}
+    for nm, sp in specs.items():  # scoring shape and split target on a sample of each code's frames
+        sample = ys[nm][:min(n_max, 32768)].cuda()
+        sizes = [b for b in (256, 4096, 32768) if b <= sample.shape[0]]
+        tuned[nm] = autotune.tune(sp.code, sample, sp.L, sp.T, batch_sizes=sizes, reps=3, use_cache=False)
     srv = serving.Server(specs, max_batch=args.serve_batch, pool_frames=4 * args.serve_batch,
                          min_batch=args.serve_batch // 8, max_wait_s=args.serve_wait_us * 1e-6,
                          pools_per_code=args.serve_pools)
@@ -667,7 +687,8 @@ def run_serving(args):
             "config": {"workload": "serving: Poisson arrivals, 50/50 RM(2,6)+CRC-6 (L=8,T=4) / RM(2,7)+CRC-6 (L=16,T=6), "
                                    "Eb/N0 U[0.5,3] dB; one stage-2 pool per code (continuous batching)",
                        "max_batch": args.serve_batch, "pool_frames": srv.slots, "pools_per_code": args.serve_pools,
-                       "max_wait_us": args.serve_wait_us, "seconds_per_rate": args.serve_seconds},
+                       "max_wait_us": args.serve_wait_us, "seconds_per_rate": args.serve_seconds,
+                       "tuned": {nm: {"shape": t["shape"], "split_items": t["value"]} for nm, t in tuned.items()}},
             "rates": out}
     print(json.dumps(line), flush=True)
 
@@ -687,6 +708,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample size in CPU seconds")
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tune", action="store_true", help="autotune the scoring shape and split target first")
     ap.add_argument("--rates", default="1,2,5,10,20", help="serving: offered M frames/s")
     ap.add_argument("--serve-seconds", type=float, default=0.1, help="serving: seconds of traffic per rate")
     ap.add_argument("--serve-batch", type=int, default=65536)

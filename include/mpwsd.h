@@ -417,9 +417,14 @@ MPWSD_API int mpwsd_profile_end(mpwsd_code *code, mpwsd_kernel_time *out);
 #define MPWSD_TUNE_SPLIT_ITEMS 0 /* tensor-core scoring: when a launch has fewer 256-row units than this, each
                                     unit's pattern tiles are split into chunks scanned by different CTAs so the
                                     launch has about this many work items; 0 = never split. Default: SMs / 2 */
-#define MPWSD_TUNE_KNOBS 1
+#define MPWSD_TUNE_TC_SHAPE 1    /* tensor-core scoring kernel shape: 0 (default) n = 64: 256-pattern tiles, two
+                                    A-builder warps, two-stage tile ring; n = 128: 128-pattern tiles, two builders,
+                                    two stages. 1: as 0 with four A-builder warps. n = 64 only: 2: 128-pattern
+                                    tiles (two accumulators per row block alternate), two stages; 3: as 2 with a
+                                    four-stage ring */
+#define MPWSD_TUNE_KNOBS 2
 
-/* Set / get a tunable (MPWSD_EINVAL for an unknown knob or a negative value). */
+/* Set / get a tunable (MPWSD_EINVAL for an unknown knob or a value outside its range). */
 MPWSD_API int mpwsd_tune_set(mpwsd_code *code, int knob, int value);
 MPWSD_API int mpwsd_tune_get(const mpwsd_code *code, int knob, int *value);
 

@@ -1,13 +1,20 @@
 """Autotuner for the launch parameters of a libmpwsd code handle.
 
-The tunable is MPWSD_TUNE_SPLIT_ITEMS: how many work items a tensor-core
-scoring launch aims at when it has few 256-row units (each unit's pattern
-tiles are then split across CTAs). The best value depends on the code (pattern
-tiles per unit), the list size, the batch sizes a caller uses and how many
-decodes run concurrently, so it is measured, not guessed: every candidate is
-timed on the caller's representative frames (CUDA graph replays, CUDA events)
-at each batch size, the candidate with the smallest summed time wins, and the
-choice is cached on disk keyed by the code, L, T, batch sizes and GPU.
+Two knobs of the tensor-core scoring kernel are tuned:
+
+* MPWSD_TUNE_TC_SHAPE -- the kernel's tile shape among the instantiated ones
+  (pattern tile 256 or 128 wide, two or four A-builder warps, a two- or
+  four-stage pattern-tile ring; see include/mpwsd.h);
+* MPWSD_TUNE_SPLIT_ITEMS -- how many work items a launch aims at when it has
+  few 256-row units (each unit's pattern tiles are then split across CTAs).
+
+The best values depend on the code (pattern tiles per unit), the list size,
+the batch sizes a caller uses and how many decodes run concurrently, so they
+are measured, not guessed: every candidate is timed on the caller's
+representative frames (CUDA graph replays, CUDA events) at each batch size and
+the one with the smallest summed time wins. The shape is chosen first (at two
+split targets), then the split target for that shape. The choice is cached on
+disk keyed by the code, L, T, batch sizes and GPU, and records both knobs.
 Tuning changes speed only; the decoded output is identical for every value.
 """
 from __future__ import annotations
@@ -59,10 +66,36 @@ def candidates(sms: int) -> list[int]:
     return sorted({0, max(1, sms // 4), max(1, sms // 2), sms, 2 * sms})
 
 
-def measure(code, y, L: int, T: int, batch_sizes, value: int, reps: int = 10) -> float:
-    """Summed mean decode time (ms) over the batch sizes with the knob at value."""
+def shapes(code: "mpwsd.Code") -> list[int]:
+    """The MPWSD_TUNE_TC_SHAPE values instantiated for this code length."""
+    out = []
+    for v in range(8):
+        try:
+            code.tune_set(mpwsd.TUNE_TC_SHAPE, v)
+        except mpwsd.MpwsdError:
+            continue
+        out.append(v)
+    code.tune_set(mpwsd.TUNE_TC_SHAPE, 0)
+    return out
+
+
+def choose(shape_list, split_list, default_split: int, run) -> tuple[int, int]:
+    """The two-pass search: the shape with the smallest time at the default
+    split target or at no split, then the split target (candidates plus the
+    default) with the smallest time for that shape; ties go to the lower
+    value. run(shape, split) returns the time of one setting."""
+    best_shape = min(shape_list, key=lambda sh: (min(run(sh, default_split), run(sh, 0)), sh))
+    best_split = min(sorted(set(split_list) | {default_split}), key=lambda v: (run(best_shape, v), v))
+    return best_shape, best_split
+
+
+def measure(code, y, L: int, T: int, batch_sizes, value: int, reps: int = 10, shape: int | None = None) -> float:
+    """Summed mean decode time (ms) over the batch sizes with the split target
+    at `value` (and the scoring shape at `shape`, if given)."""
     import torch
 
+    if shape is not None:
+        code.tune_set(mpwsd.TUNE_TC_SHAPE, shape)
     code.tune_set(mpwsd.TUNE_SPLIT_ITEMS, value)
     total = 0.0
     for B in batch_sizes:
@@ -86,9 +119,10 @@ def measure(code, y, L: int, T: int, batch_sizes, value: int, reps: int = 10) ->
 
 def tune(code: "mpwsd.Code", y, L: int, T: int, batch_sizes=(256, 2048, 16384), use_cache: bool = True,
          reps: int = 10) -> dict:
-    """Choose MPWSD_TUNE_SPLIT_ITEMS for `code` from the representative frames
-    `y` (CUDA float32 tensor, at least max(batch_sizes) rows), apply it to the
-    handle and return {"value", "times_ms", "cached"}."""
+    """Choose the scoring shape and split target for `code` from the
+    representative frames `y` (CUDA float32 tensor, at least max(batch_sizes)
+    rows), apply them to the handle and return {"shape", "value", "times_ms",
+    "default_ms", "cached"}; times_ms maps "shape/split" to the summed time."""
     import torch
 
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
@@ -100,15 +134,29 @@ def tune(code: "mpwsd.Code", y, L: int, T: int, batch_sizes=(256, 2048, 16384), 
     path = cache_path()
     with _lock:
         cache = _load_cache(path) if use_cache else {}
-        if key in cache:
-            code.tune_set(mpwsd.TUNE_SPLIT_ITEMS, int(cache[key]["value"]))
-            return {"value": int(cache[key]["value"]), "times_ms": cache[key]["times_ms"], "cached": True}
-    times = {v: measure(code, y, L, T, batch_sizes, v, reps) for v in candidates(sms)}
-    best = min(times, key=lambda v: (times[v], v))
-    code.tune_set(mpwsd.TUNE_SPLIT_ITEMS, best)
+        ent = cache.get(key)
+        if ent and "shape" in ent:
+            code.tune_set(mpwsd.TUNE_TC_SHAPE, int(ent["shape"]))
+            code.tune_set(mpwsd.TUNE_SPLIT_ITEMS, int(ent["value"]))
+            return {"shape": int(ent["shape"]), "value": int(ent["value"]), "times_ms": ent["times_ms"],
+                    "default_ms": ent.get("default_ms"), "cached": True}
+    default_split = code.tune_get(mpwsd.TUNE_SPLIT_ITEMS)
+    times = {}
+
+    def run(shape, split):
+        k = f"{shape}/{split}"
+        if k not in times:
+            times[k] = measure(code, y, L, T, batch_sizes, split, reps, shape=shape)
+        return times[k]
+
+    default_ms = run(0, default_split)
+    best_shape, best_split = choose(shapes(code), candidates(sms), default_split, run)
+    code.tune_set(mpwsd.TUNE_TC_SHAPE, best_shape)
+    code.tune_set(mpwsd.TUNE_SPLIT_ITEMS, best_split)
+    out = {"shape": best_shape, "value": best_split, "times_ms": dict(times), "default_ms": default_ms}
     if use_cache:
         with _lock:
             cache = _load_cache(path)
-            cache[key] = {"value": best, "times_ms": {str(k): v for k, v in times.items()}}
+            cache[key] = out
             _store_cache(path, cache)
-    return {"value": best, "times_ms": {str(k): v for k, v in times.items()}, "cached": False}
+    return dict(out, cached=False)

@@ -116,6 +116,7 @@ struct CodeDev {
     unsigned long long wait_limit_ns = 2000000000ull;
     int test_stall = 0;
     int split_items = 0;  // MPWSD_TUNE_SPLIT_ITEMS (0: no pattern split)
+    int tc_shape = 0;     // MPWSD_TUNE_TC_SHAPE: instantiated shape of the tensor-core scoring kernel
 };
 
 struct SclArgs {
@@ -199,6 +200,11 @@ cudaError_t launch_score_tc(const CodeDev &c, const ScoreArgs &a, cudaStream_t s
 // y (B x n) -> bf16 hi / lo words and ||y||_1 per frame, for direct-mode tensor-core scoring
 cudaError_t launch_split_prep(const CodeDev &c, const float *y, int64_t B, uint32_t *yhl, float *l1, cudaStream_t s);
 bool score_tc_supported(const CodeDev &c);
+// Shapes of the tensor-core scoring kernel (MPWSD_TUNE_TC_SHAPE): 0 is the
+// default of each code length, the others are compiled in score_tc_alt.cu.
+constexpr int kTcShapes = 4;
+bool tc_shape_valid(int n, int shape);
+cudaError_t launch_score_tc_alt(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
 int rm_specialisation(int n, uint64_t lo, uint64_t hi);
 cudaError_t launch_hop(const CodeDev &c, const Workspace &ws, int iter, int L, const float *y, cudaStream_t s);
 cudaError_t launch_rescan(const CodeDev &c, const Workspace &ws, int iter, int L, const float *y, cudaStream_t s);

@@ -1006,12 +1006,19 @@ extern "C" int mpwsd_profile_end(mpwsd_code *code, mpwsd_kernel_time *out) {
 
 extern "C" int mpwsd_tune_set(mpwsd_code *code, int knob, int value) {
     if (!code) return fail(MPWSD_EINVAL, "code is NULL");
-    if (knob != MPWSD_TUNE_SPLIT_ITEMS) return fail(MPWSD_EINVAL, "unknown knob %d", knob);
-    // units x chunks stays below kSplitItemsPerSm x SMs, the size of the split buffers
-    const int cap = kSplitItemsPerSm / 2 * code->d.num_sms;
-    if (value < 0 || value > cap) return fail(MPWSD_EINVAL, "split items %d outside 0..%d", value, cap);
+    if (knob == MPWSD_TUNE_SPLIT_ITEMS) {
+        // units x chunks stays below kSplitItemsPerSm x SMs, the size of the split buffers
+        const int cap = kSplitItemsPerSm / 2 * code->d.num_sms;
+        if (value < 0 || value > cap) return fail(MPWSD_EINVAL, "split items %d outside 0..%d", value, cap);
+    } else if (knob == MPWSD_TUNE_TC_SHAPE) {
+        if (!tc_shape_valid(code->d.n, value))
+            return fail(MPWSD_EINVAL, "scoring shape %d is not instantiated for n = %d", value, code->d.n);
+    } else {
+        return fail(MPWSD_EINVAL, "unknown knob %d", knob);
+    }
     std::lock_guard<std::mutex> lk(code->mu);
-    code->d.split_items = value;
+    if (knob == MPWSD_TUNE_SPLIT_ITEMS) code->d.split_items = value;
+    else code->d.tc_shape = value;
     for (auto &g : code->graphs) cudaGraphExecDestroy(g.exec);  // recorded with the old value
     code->graphs.clear();
     return MPWSD_OK;
@@ -1019,8 +1026,9 @@ extern "C" int mpwsd_tune_set(mpwsd_code *code, int knob, int value) {
 
 extern "C" int mpwsd_tune_get(const mpwsd_code *code, int knob, int *value) {
     if (!code || !value) return fail(MPWSD_EINVAL, "NULL argument");
-    if (knob != MPWSD_TUNE_SPLIT_ITEMS) return fail(MPWSD_EINVAL, "unknown knob %d", knob);
-    *value = code->d.split_items;
+    if (knob == MPWSD_TUNE_SPLIT_ITEMS) *value = code->d.split_items;
+    else if (knob == MPWSD_TUNE_TC_SHAPE) *value = code->d.tc_shape;
+    else return fail(MPWSD_EINVAL, "unknown knob %d", knob);
     return MPWSD_OK;
 }
 

@@ -26,6 +26,7 @@ FLAG_STAGE2, FLAG_CRC_OK, FLAG_RESCAN, FLAG_ERROR = 0x1, 0x2, 0x4, 0x100
 ITERS_SHIFT = 4
 MAX_L, MAX_T, TOPK = 32, 15, 4
 TUNE_SPLIT_ITEMS = 0
+TUNE_TC_SHAPE = 1
 
 _lock = threading.Lock()
 _lib = None

@@ -72,22 +72,31 @@ def test_serving_admission_by_memory():
         tiny.run(arrivals, ys)
 
 
-def test_autotune_picks_a_candidate_and_output_is_unchanged(tmp_path, monkeypatch):
+@pytest.mark.parametrize("m,crc_code,weights,L,T", [(7, "rm27_crc6", [32], 16, 6), (6, "rm26_crc6", [16], 8, 4)])
+def test_autotune_picks_a_candidate_and_output_is_unchanged(tmp_path, monkeypatch, m, crc_code, weights, L, T):
     mp = cuda_or_skip()
     from paper_2602_08501_gb300 import autotune
 
     monkeypatch.setenv("MPWSD_TUNE_CACHE", str(tmp_path / "tune.json"))
-    code = mp.Code.rm(7, 2, crc_poly=0x21, crc_len=6, weights=[32])
-    wl = synth.make_workload("rm27_crc6", 1.5, 4096, seed=70)
+    code = mp.Code.rm(m, 2, crc_poly=0x21, crc_len=6, weights=weights)
+    wl = synth.make_workload(crc_code, 1.5, 4096, seed=70)
     y = torch.from_numpy(wl.y).cuda()
-    outs = {}
-    for v in (0, 16, 76, 152):
-        code.tune_set(mp.TUNE_SPLIT_ITEMS, v)
-        cw, fl = code.decode(y, 16, 6)
-        torch.cuda.synchronize()
-        outs[v] = (cw.clone(), fl.clone())
-    for v in outs:
-        assert torch.equal(outs[v][0], outs[0][0]) and torch.equal(outs[v][1], outs[0][1])
-    r = autotune.tune(code, y, 16, 6, batch_sizes=(256, 4096), reps=3)
+    shapes = autotune.shapes(code)
+    assert shapes == ([0, 1, 2, 3] if m == 6 else [0, 1])
+    ref = None
+    for sh in shapes:
+        for v in (0, 16, 76, 152):
+            code.tune_set(mp.TUNE_TC_SHAPE, sh)
+            code.tune_set(mp.TUNE_SPLIT_ITEMS, v)
+            cw, fl = code.decode(y, L, T)
+            torch.cuda.synchronize()
+            if ref is None:
+                ref = (cw.clone(), fl.clone())
+            assert torch.equal(cw, ref[0]) and torch.equal(fl, ref[1]), (sh, v)
+    with pytest.raises(mp.MpwsdError):
+        code.tune_set(mp.TUNE_TC_SHAPE, 9)
+    r = autotune.tune(code, y, L, T, batch_sizes=(256, 4096), reps=3)
     assert not r["cached"] and code.tune_get(mp.TUNE_SPLIT_ITEMS) == r["value"]
-    assert autotune.tune(code, y, 16, 6, batch_sizes=(256, 4096), reps=3)["cached"]
+    assert code.tune_get(mp.TUNE_TC_SHAPE) == r["shape"] in shapes
+    assert r["times_ms"][f"{r['shape']}/{r['value']}"] <= r["default_ms"]
+    assert autotune.tune(code, y, L, T, batch_sizes=(256, 4096), reps=3)["cached"]
