@@ -541,6 +541,15 @@ def run_ours(args, wl_cfg):
             return {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "Tadd/s",
                     "frac": ach / (alu_peak / 1e12), "traffic": None, "kernel": "score_fp32",
                     "peak_kind": "152 SMs x 128 FP32 lanes x max SM clock"}
+        if kname == "score_flats":
+            # the transform's additions: n log2 n per row, then kd 2^kd per complement (kd = m - log2 w)
+            kd = wl_cfg["m"] - int(math.log2(wmax))
+            adds = evals / P * (n * math.log2(n) + (P >> kd) * kd * (1 << kd)) / launches
+            ach = adds / per_launch_s / 1e12
+            return {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "Tadd/s",
+                    "frac": ach / (alu_peak / 1e12), "traffic": None, "kernel": "score_flats",
+                    "peak_kind": "152 SMs x 128 INT32 lanes x max SM clock",
+                    "adds_per_launch": adds, "pattern_sums_per_s": evals / launches / per_launch_s}
         if kname == "scl":
             ops = frames * 4 * L * n * math.log2(n)  # per launch (one per step): Table I, (4/3) L log2 N ED units x 3N
             ach = ops / per_launch_s / 1e12
@@ -584,12 +593,14 @@ def run_ours(args, wl_cfg):
                 "kernel": kname}
 
     roof = roofline_for(dominant)
-    others = [roofline_for(k) for k in ("scl", "osd", "score_tc", "score_fp32", "hop") if k in kinds and k != dominant]
+    others = [roofline_for(k) for k in ("scl", "osd", "score_tc", "score_fp32", "score_flats", "hop")
+              if k in kinds and k != dominant]
 
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x2+f64" if args.mode == "bf16x2" else "f32+f64", "data": "synthetic",
+        "vs_baseline": None, "data": "synthetic",
+        "dtype": {"bf16x2": "bf16x2+f64", "fp32": "f32+f64", "flats": "i32+f64"}[args.mode],
         "config": workload_config(wl_cfg, args, world),
         "pattern_evals_per_s": {
             "scored": total_evals / timed_s,
@@ -701,7 +712,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving"], default="rm26_crc6_1db")
-    ap.add_argument("--mode", choices=["bf16x2", "fp32"], default=None)
+    ap.add_argument("--mode", choices=["bf16x2", "fp32", "flats"], default=None)
     ap.add_argument("--frames", type=int, default=0, help="override frames per step")
     ap.add_argument("--ebn0", type=float, default=None, help="override the workload's Eb/N0 (dB)")
     ap.add_argument("--seed", type=int, default=None, help="override the workload's seed")

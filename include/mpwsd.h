@@ -67,6 +67,10 @@ extern "C" {
 /* ---- options ------------------------------------------------------------ */
 #define MPWSD_SCORE_BF16X2 0    /* tcgen05 tensor cores, y split into bf16 hi + lo, FP32 accumulate */
 #define MPWSD_SCORE_FP32 1      /* FP32 CUDA cores, sparse gather-add over each pattern's support */
+#define MPWSD_SCORE_FLATS 2     /* exact integer scores from Walsh-Hadamard coefficients, for pattern sets made
+                                   of all cosets of subspaces whose complements have dimension 1 or 2 (the
+                                   minimum-weight codewords of RM(1, m) and RM(2, m)); MPWSD_EUNSUPPORTED
+                                   for other pattern sets */
 
 #define MPWSD_RULE_TOP1 0       /* stage 1 succeeds iff the best-metric list entry passes the CRC (Sec. III-A) */
 #define MPWSD_RULE_ANY 1        /* stage 1 succeeds with the best-metric entry that passes the CRC */
@@ -84,7 +88,7 @@ extern "C" {
 #define MPWSD_FLAG_ERROR 0x0100u    /* a device-side wait timed out; the frame's output is not valid */
 
 typedef struct mpwsd_opts {
-    int score_mode;  /* MPWSD_SCORE_BF16X2 (default) or MPWSD_SCORE_FP32 */
+    int score_mode;  /* MPWSD_SCORE_BF16X2 (default), MPWSD_SCORE_FP32 or MPWSD_SCORE_FLATS */
     int stage1_rule; /* MPWSD_RULE_TOP1 (default) or MPWSD_RULE_ANY */
     int always_on;   /* nonzero: run stage 2 on every frame, CRC or not (always-on mode, Sec. III-C) */
     int use_graph;   /* nonzero: replay the decode's launch sequence as a CUDA graph. The first call with a
@@ -396,7 +400,8 @@ MPWSD_API int mpwsd_sync(mpwsd_code *code, void *stream);
 #define MPWSD_KERNEL_RESCAN 4     /* full FP64 rescan of overflowing rows */
 #define MPWSD_KERNEL_FINAL 5      /* per-frame argmin ED + flags */
 #define MPWSD_KERNEL_OSD 6        /* stage 1 by OSD(order) + CRC + compaction */
-#define MPWSD_KERNEL_KINDS 7
+#define MPWSD_KERNEL_SCORE_FLATS 7 /* scoring, exact Walsh-Hadamard coset sums (MPWSD_SCORE_FLATS) */
+#define MPWSD_KERNEL_KINDS 8
 
 typedef struct mpwsd_kernel_time {
     int64_t launches; /* kernels of this class launched while profiling */

@@ -11,7 +11,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <array>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <string>
 #include <unordered_set>
@@ -173,6 +175,8 @@ static void free_code_device(CodeDev &d) {
     cudaFree(d.pat_bits);
     cudaFree(d.pat_supp);
     cudaFree(d.pat_tiles);
+    cudaFree(d.flat_off);
+    cudaFree(d.flat_idx);
     cudaFree(d.crc_masks);
     cudaFree(d.gen_rows);
     cudaFree(d.osd_sets);
@@ -180,10 +184,83 @@ static void free_code_device(CodeDev &d) {
     d.pat_bits = nullptr;
     d.pat_supp = nullptr;
     d.pat_tiles = nullptr;
+    d.flat_off = nullptr;
+    d.flat_idx = nullptr;
     d.crc_masks = nullptr;
     d.gen_rows = nullptr;
     d.osd_sets = nullptr;
     d.stats = nullptr;
+}
+
+// Flat structure of a pattern set for MPWSD_SCORE_FLATS. Positions j are read
+// as m-bit vectors (the binary digits of j, the coordinates of the Arikan
+// form). Returns the complement dimension kd (1 or 2) and fills the entries
+// (see CodeDev::flat_off / flat_idx) when every pattern is a coset a + V of a
+// linear subspace V, all of one dimension m - kd, and every coset of every V
+// that occurs is in the set; returns 0 otherwise.
+static int flats_table(int n, int m, const uint64_t *patterns, int64_t P, int W, std::vector<uint2> &off,
+                       std::vector<int32_t> &idx) {
+    off.clear();
+    idx.clear();
+    if (P < 1 || n > 128) return 0;
+    auto bit = [&](int64_t p, int j) { return (int)((patterns[p * W + j / 64] >> (j % 64)) & 1ull); };
+    auto parity = [](int x) { return __builtin_parity((unsigned)x); };
+    int kd = -1;
+    std::map<std::vector<int>, int> entry_of;  // complement (its nonzero elements, ascending) -> entry
+    std::vector<std::array<int, 2>> basis;
+    for (int64_t p = 0; p < P; ++p) {
+        std::vector<int> pts;
+        for (int j = 0; j < n; ++j)
+            if (bit(p, j)) pts.push_back(j);
+        const size_t sz = pts.size();
+        if (sz == 0 || (sz & (sz - 1))) return 0;
+        int dim = 0;
+        while ((1u << dim) < sz) ++dim;
+        const int a = pts[0];
+        std::vector<char> inV((size_t)n, 0);
+        for (int x : pts) inV[(size_t)(x ^ a)] = 1;
+        for (int x : pts)  // V = pts ^ a is closed under XOR
+            for (int y : pts)
+                if (!inV[(size_t)(x ^ y)]) return 0;
+        const int this_kd = m - dim;
+        if (this_kd < 1 || this_kd > 2) return 0;
+        if (kd < 0) kd = this_kd;
+        if (kd != this_kd) return 0;
+        std::vector<int> comp;  // w != 0 orthogonal to every element of V
+        for (int w = 1; w < n; ++w) {
+            bool ok = true;
+            for (int x : pts)
+                if (parity(w & (x ^ a))) {
+                    ok = false;
+                    break;
+                }
+            if (ok) comp.push_back(w);
+        }
+        if ((int)comp.size() != (1 << kd) - 1) return 0;
+        auto it = entry_of.find(comp);
+        int e;
+        if (it == entry_of.end()) {
+            e = (int)basis.size();
+            entry_of.emplace(comp, e);
+            basis.push_back({comp[0], kd == 2 ? comp[1] : 0});
+            idx.insert(idx.end(), 4, -1);
+        } else {
+            e = it->second;
+        }
+        const int c1 = parity(basis[(size_t)e][0] & a), c2 = kd == 2 ? parity(basis[(size_t)e][1] & a) : 0;
+        int32_t &slot = idx[(size_t)e * 4 + c1 + 2 * c2];
+        if (slot >= 0) return 0;  // the same coset twice
+        slot = (int32_t)p;
+    }
+    for (size_t e = 0; e < basis.size(); ++e)  // every coset present
+        for (int c = 0; c < (1 << kd); ++c)
+            if (idx[e * 4 + (size_t)c] < 0) return 0;
+    const unsigned stride = (unsigned)kFlatsThreads * 4u;  // bytes between Z(w) and Z(w + 1) of one thread
+    for (auto &b : basis) {
+        const unsigned w1 = (unsigned)b[0], w2 = (unsigned)b[1];
+        off.push_back(make_uint2(w1 * stride | ((w2 * stride) << 16), (w1 ^ w2) * stride));
+    }
+    return kd;
 }
 
 extern "C" int mpwsd_load_code(int n, const uint8_t *G, const uint8_t *frozen, int k_info, uint32_t crc_poly,
@@ -370,12 +447,19 @@ extern "C" int mpwsd_load_code(int n, const uint8_t *G, const uint8_t *frozen, i
             }
         }
     }
+    // flat structure of the pattern set (MPWSD_SCORE_FLATS)
+    std::vector<uint2> flat_off;
+    std::vector<int32_t> flat_idx;
+    d.flat_kd = flats_table(n, m, patterns, n_patterns, W, flat_off, flat_idx);
+    d.n_flat = d.flat_kd ? (int)flat_off.size() : 0;
     // device images
     struct Up {
         void **dst;
         const void *src;
         size_t bytes;
     } ups[] = {
+        {(void **)&d.flat_off, flat_off.data(), flat_off.size() * sizeof(uint2)},
+        {(void **)&d.flat_idx, flat_idx.data(), flat_idx.size() * 4},
         {(void **)&d.pat_bits, patterns, (size_t)n_patterns * W * 8},
         {(void **)&d.pat_supp, supp.data(), supp.size() * 4},
         {(void **)&d.pat_tiles, tiles.data(), tiles.size() * 2},
@@ -531,7 +615,8 @@ static int check_opts(const mpwsd_opts *opts, mpwsd_opts *o) {
     memset(o, 0, sizeof(*o));
     if (!opts) return MPWSD_OK;
     *o = *opts;
-    if (o->score_mode != MPWSD_SCORE_BF16X2 && o->score_mode != MPWSD_SCORE_FP32)
+    if (o->score_mode != MPWSD_SCORE_BF16X2 && o->score_mode != MPWSD_SCORE_FP32 &&
+        o->score_mode != MPWSD_SCORE_FLATS)
         return fail(MPWSD_EINVAL, "score_mode = %d", o->score_mode);
     if (o->stage1_rule != MPWSD_RULE_TOP1 && o->stage1_rule != MPWSD_RULE_ANY)
         return fail(MPWSD_EINVAL, "stage1_rule = %d", o->stage1_rule);
@@ -557,6 +642,8 @@ static int check_device(const mpwsd_code *code) {
 static cudaError_t launch_score(mpwsd_code *code, int mode, const ScoreArgs &a, cudaStream_t s) {
     if (mode == MPWSD_SCORE_FP32)
         return timed_launch(code, MPWSD_KERNEL_SCORE_FP32, s, [&] { return launch_score_fp32(code->d, a, s); });
+    if (mode == MPWSD_SCORE_FLATS)
+        return timed_launch(code, MPWSD_KERNEL_SCORE_FLATS, s, [&] { return launch_score_flats(code->d, a, s); });
     return timed_launch(code, MPWSD_KERNEL_SCORE_TC, s, [&] { return launch_score_tc(code->d, a, s); });
 }
 
@@ -750,6 +837,9 @@ static int check_decode_args(mpwsd_code *code, const float *y_dev, int64_t B, in
     if (st) return st;
     if (o->score_mode == MPWSD_SCORE_BF16X2 && !score_tc_supported(code->d))
         return fail(MPWSD_EUNSUPPORTED, "BF16X2 tensor-core scoring needs n = 64 or 128");
+    if (o->score_mode == MPWSD_SCORE_FLATS && code->d.n_flat == 0)
+        return fail(MPWSD_EUNSUPPORTED, "FLATS scoring needs a pattern set made of all cosets of subspaces whose "
+                                        "complements have dimension 1 or 2");
     if (o->stage1 == MPWSD_STAGE1_OSD && code->d.k > 32)
         return fail(MPWSD_EUNSUPPORTED, "OSD stage 1 needs k <= 32 (k = %d)", code->d.k);
     return check_device(code);
@@ -896,10 +986,12 @@ extern "C" int mpwsd_score_topk(mpwsd_code *code, int score_mode, const float *y
                                 const int32_t *frame_dev, const uint64_t *cw_dev, int64_t M, float *topk_val_dev,
                                 int32_t *topk_idx_dev, void *stream) {
     if (!code) return fail(MPWSD_EINVAL, "code is NULL");
-    if (score_mode != MPWSD_SCORE_BF16X2 && score_mode != MPWSD_SCORE_FP32)
+    if (score_mode != MPWSD_SCORE_BF16X2 && score_mode != MPWSD_SCORE_FP32 && score_mode != MPWSD_SCORE_FLATS)
         return fail(MPWSD_EINVAL, "score_mode = %d", score_mode);
     if (score_mode == MPWSD_SCORE_BF16X2 && !score_tc_supported(code->d))
         return fail(MPWSD_EUNSUPPORTED, "BF16X2 tensor-core scoring needs n = 64 or 128");
+    if (score_mode == MPWSD_SCORE_FLATS && code->d.n_flat == 0)
+        return fail(MPWSD_EUNSUPPORTED, "FLATS scoring needs a pattern set of whole cosets of subspaces");
     if (M < 0 || B < 0 || M > 0x7fffffffLL || (M > 0 && B == 0)) return fail(MPWSD_EINVAL, "bad sizes");
     if (M > 0 && (!y_dev || !frame_dev || !cw_dev || !topk_val_dev || !topk_idx_dev))
         return fail(MPWSD_EINVAL, "NULL buffer");

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libmpwsd.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "mpwsd.h")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
-SCORE_BF16X2, SCORE_FP32 = 0, 1
+SCORE_BF16X2, SCORE_FP32, SCORE_FLATS = 0, 1, 2
 RULE_TOP1, RULE_ANY = 0, 1
 STAGE1_SCL, STAGE1_OSD = 0, 1
 FLAG_STAGE2, FLAG_CRC_OK, FLAG_RESCAN, FLAG_ERROR = 0x1, 0x2, 0x4, 0x100
@@ -48,7 +48,7 @@ class _KTime(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 
-KERNEL_NAMES = ("scl", "score_tc", "score_fp32", "hop", "rescan", "final", "osd")
+KERNEL_NAMES = ("scl", "score_tc", "score_fp32", "hop", "rescan", "final", "osd", "score_flats")
 
 
 class _Stats(ctypes.Structure):
@@ -229,7 +229,7 @@ class Code:
     @staticmethod
     def _opts(score_mode, rule, always_on, use_graph=False, osd_order=None):
         o = _Opts()
-        o.score_mode = {"bf16x2": SCORE_BF16X2, "fp32": SCORE_FP32}.get(score_mode, score_mode)
+        o.score_mode = {"bf16x2": SCORE_BF16X2, "fp32": SCORE_FP32, "flats": SCORE_FLATS}.get(score_mode, score_mode)
         o.stage1_rule = {"top1": RULE_TOP1, "any": RULE_ANY}.get(rule, rule)
         o.always_on = int(bool(always_on))
         o.use_graph = int(bool(use_graph))
@@ -311,7 +311,7 @@ class Code:
         M = int(frame.shape[0])
         vals = torch.empty((M, TOPK), dtype=torch.float32, device=y.device)
         idx = torch.empty((M, TOPK), dtype=torch.int32, device=y.device)
-        mode = {"bf16x2": SCORE_BF16X2, "fp32": SCORE_FP32}.get(score_mode, score_mode)
+        mode = {"bf16x2": SCORE_BF16X2, "fp32": SCORE_FP32, "flats": SCORE_FLATS}.get(score_mode, score_mode)
         _check(lib().mpwsd_score_topk(self._h, int(mode), _dev(y, torch.float32, "y"), int(y.shape[0]),
                                       _dev(frame, torch.int32, "frame"), _dev(cw, torch.int64, "cw"), M,
                                       _dev(vals, torch.float32, "vals"), _dev(idx, torch.int32, "idx"),
