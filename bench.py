@@ -527,8 +527,8 @@ def run_ours(args, wl_cfg):
         if kname == "score_tc":
             flops = evals * 2 * n * 2 / launches  # dense bf16 work per launch: 2 n flops x 2 splits per pattern-eval
             ach = flops / per_launch_s / 1e12
-            src = src_hash("paper_2602_08501_gb300/csrc/score_tc.cu", "paper_2602_08501_gb300/csrc/common.cuh",
-                           "paper_2602_08501_gb300/csrc/internal.h")
+            src = src_hash("paper_2602_08501_gb300/csrc/score_tc.cu", "paper_2602_08501_gb300/csrc/score_tc_impl.cuh",
+                           "paper_2602_08501_gb300/csrc/common.cuh", "paper_2602_08501_gb300/csrc/internal.h")
             bpr = recorded_traffic("score_tc", src, "row")
             tr = None if bpr is None else bpr * (evals / P) / launches  # scaled by active rows per launch
             return {"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s",
@@ -546,8 +546,13 @@ def run_ours(args, wl_cfg):
             kd = wl_cfg["m"] - int(math.log2(wmax))
             adds = evals / P * (n * math.log2(n) + (P >> kd) * kd * (1 << kd)) / launches
             ach = adds / per_launch_s / 1e12
+            src = src_hash("paper_2602_08501_gb300/csrc/score_flats.cu", "paper_2602_08501_gb300/csrc/common.cuh",
+                           "paper_2602_08501_gb300/csrc/internal.h")
+            bpr = recorded_traffic("score_flats", src, "row")
+            tr = None if bpr is None else bpr * (evals / P) / launches
             return {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "Tadd/s",
-                    "frac": ach / (alu_peak / 1e12), "traffic": None, "kernel": "score_flats",
+                    "frac": ach / (alu_peak / 1e12), "traffic": tr, "traffic_source": traffic_note,
+                    "kernel": "score_flats",
                     "peak_kind": "152 SMs x 128 INT32 lanes x max SM clock",
                     "adds_per_launch": adds, "pattern_sums_per_s": evals / launches / per_launch_s}
         if kname == "scl":
@@ -568,7 +573,8 @@ def run_ours(args, wl_cfg):
             ach = ops / per_launch_s / 1e12
             src = src_hash("paper_2602_08501_gb300/csrc/osd.cu", "paper_2602_08501_gb300/csrc/common.cuh",
                            "paper_2602_08501_gb300/csrc/internal.h")
-            bpf = recorded_traffic("osd", src, "frame")
+            # the recorded capture is of the always-on workload (every frame writes trajectories)
+            bpf = recorded_traffic("osd", src, "frame") if aom else None
             tr = None if bpf is None else bpf * frames
             return {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "Top/s",
                     "frac": ach / (alu_peak / 1e12), "traffic": tr, "traffic_source": traffic_note, "kernel": "osd",

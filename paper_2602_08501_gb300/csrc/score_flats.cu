@@ -18,9 +18,10 @@
 // Mapping: one thread per row. The row's z goes through the transform in
 // registers; the coefficients are stored to shared memory with the thread
 // index innermost (conflict-free), and the loop over the complements reads
-// them at the byte offsets stored in the code's table (uniform across the
-// warp; 8 bytes an entry, so that the table stays in L1 beside the shared
-// memory). Z(0) is common to the 2^kd sums of a complement and the smallest of
+// them at the byte offsets stored in the code's table, which each CTA first
+// copies to shared memory, unpacked to one 32-bit offset per coefficient (16
+// bytes an entry, so the loop spends no instruction on unpacking; every lane
+// reads the same entry, a broadcast). Z(0) is common to the 2^kd sums of a complement and the smallest of
 // them is Z(0) + min(Z(w1) - |Z(w2) + Z(w1^w2)|, -Z(w1) - |Z(w2) - Z(w1^w2)|)
 // (Z(0) - |Z(w1)| for kd = 1), so pass 1 takes that minimum relative to Z(0),
 // keeping the smallest value, the first complement that reaches it and
@@ -60,8 +61,13 @@ __global__ void __launch_bounds__(kFT) score_flats_kernel(const ScoreArgs a, con
     const int nrows = a.n_rows_dev ? *a.n_rows_dev : (int)a.n_rows;
     const int tid = threadIdx.x;
     const char *zb = reinterpret_cast<const char *>(zs + tid);
-    const uint2 *tab = c.flat_off;
     const int ne = c.n_flat;
+    uint4 *tab = reinterpret_cast<uint4 *>(zs + N * kFT);  // the complement table, after the coefficients
+    for (int e = tid; e < ne; e += kFT) {
+        const uint2 q = c.flat_off[e];
+        tab[e] = make_uint4(q.x & 0xffffu, q.x >> 16, q.y, 0u);
+    }
+    __syncthreads();
     for (int r = blockIdx.x * kFT + tid; r < nrows; r += gridDim.x * kFT) {
         const int t = a.rows ? a.rows[r] : r;
         const int fr = a.row_frame ? a.row_frame[r] : a.slot_frame[t / a.L];
@@ -98,12 +104,12 @@ __global__ void __launch_bounds__(kFT) score_flats_kernel(const ScoreArgs a, con
         int best = INT_MAX, be = 0;
         bool tie = false;
         for (int e = 0; e < ne; ++e) {
-            const uint2 o = __ldg(tab + e);
-            const int z1 = *reinterpret_cast<const int *>(zb + (o.x & 0xffffu));
+            const uint4 o = tab[e];
+            const int z1 = *reinterpret_cast<const int *>(zb + o.x);
             int m;
             if constexpr (KD == 2) {
-                const int z2 = *reinterpret_cast<const int *>(zb + (o.x >> 16));
-                const int z3 = *reinterpret_cast<const int *>(zb + o.y);
+                const int z2 = *reinterpret_cast<const int *>(zb + o.y);
+                const int z3 = *reinterpret_cast<const int *>(zb + o.z);
                 m = min(z1 - abs(z2 + z3), -z1 - abs(z2 - z3));
             } else {
                 m = -abs(z1);
@@ -117,10 +123,10 @@ __global__ void __launch_bounds__(kFT) score_flats_kernel(const ScoreArgs a, con
         int bi = INT_MAX;
         const int e0 = tie ? 0 : be, e1 = tie ? ne : be + 1;
         for (int e = e0; e < e1; ++e) {
-            const uint2 o = __ldg(tab + e);
-            const int z1 = *reinterpret_cast<const int *>(zb + (o.x & 0xffffu));
-            const int z2 = KD == 2 ? *reinterpret_cast<const int *>(zb + (o.x >> 16)) : 0;
-            const int z3 = KD == 2 ? *reinterpret_cast<const int *>(zb + o.y) : 0;
+            const uint4 o = tab[e];
+            const int z1 = *reinterpret_cast<const int *>(zb + o.x);
+            const int z2 = KD == 2 ? *reinterpret_cast<const int *>(zb + o.y) : 0;
+            const int z3 = KD == 2 ? *reinterpret_cast<const int *>(zb + o.z) : 0;
             int s[4];
             coset_sums<KD>(z0, z1, z2, z3, s[0], s[1], s[2], s[3]);
             const int4 ix = __ldg(reinterpret_cast<const int4 *>(c.flat_idx) + e);
@@ -143,10 +149,13 @@ __global__ void __launch_bounds__(kFT) score_flats_kernel(const ScoreArgs a, con
 
 template <int N, int KD>
 cudaError_t launch_nk(const CodeDev &c, const ScoreArgs &a, cudaStream_t s) {
-    constexpr int smem = N * kFT * 4;
+    const int smem = N * kFT * 4 + c.n_flat * 16;
     cudaError_t e = cudaFuncSetAttribute(score_flats_kernel<N, KD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    int64_t grid = (int64_t)c.num_sms * (N >= 128 ? 3 : 6);
+    int per_sm = 0;  // CTAs that fit on an SM beside each other (registers, shared memory)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, score_flats_kernel<N, KD>, kFT, smem);
+    if (e != cudaSuccess) return e;
+    int64_t grid = (int64_t)c.num_sms * std::max(per_sm, 1);
     if (!a.n_rows_dev) grid = std::min<int64_t>(grid, (a.n_rows + kFT - 1) / kFT);
     if (grid <= 0) return cudaSuccess;
     score_flats_kernel<N, KD><<<(unsigned)grid, kFT, smem, s>>>(a, c);
