@@ -54,16 +54,17 @@ def _alloc_child(q):
     from paper_2602_08501_gb300 import mpwsd
 
     out = {}
-    # device allocations 1..7: pattern bits, supports, tiles, CRC masks, generator rows, OSD row sets, stats
+    # device allocations 1..9: flats table (offsets, pattern indices), pattern bits, supports, tiles, CRC
+    # masks, generator rows, OSD row sets, stats
     code = mpwsd.Code.rm(6, 2, crc_poly=0x21, crc_len=6, weights=[16])
     wl = synth.make_workload("rm26_crc6", 1.0, 500, seed=32)
     y = th.from_numpy(wl.y).cuda()
     try:
-        code.decode(y, 8, 4)  # allocation 8 (the handle's workspace) fails
+        code.decode(y, 8, 4)  # allocation 10 (the handle's workspace) fails
         out["first"] = "ok"
     except mpwsd.MpwsdError as e:
         out["first"] = e.status
-    cw, fl = code.decode(y, 8, 4)  # allocation 9 succeeds
+    cw, fl = code.decode(y, 8, 4)  # allocation 11 succeeds
     code.sync()
     cw2, fl2 = code.decode(y, 8, 4, score_mode="fp32")
     code.sync()
@@ -76,7 +77,7 @@ def test_injected_allocation_failure_returns_enomem():
     ctx = mproc.get_context("spawn")
     q = ctx.Queue()
     env_old = os.environ.get("MPWSD_TEST_FAIL_ALLOC")
-    os.environ["MPWSD_TEST_FAIL_ALLOC"] = "8"
+    os.environ["MPWSD_TEST_FAIL_ALLOC"] = "10"
     try:
         p = ctx.Process(target=_alloc_child, args=(q,))
         p.start()
