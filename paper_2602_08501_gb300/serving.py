@@ -172,6 +172,8 @@ class Server:
         batch_sizes = []
         for nm in names:
             self.specs[nm].code.reset_stats()
+        # events are made up front (one per submission or step at most), so the loop allocates nothing
+        ev_free = [torch.cuda.Event(enable_timing=True) for _ in range(2 * sum(total.values()) // 64 + 4096)]
         ref = torch.cuda.Event(enable_timing=True)
         ref.record(torch.cuda.current_stream())
         torch.cuda.synchronize()
@@ -192,17 +194,23 @@ class Server:
                 oldest = arrivals[nm][sub[nm]]
                 if not (pend >= self.min_batch or now - oldest >= self.max_wait_s or arrived == total[nm]):
                     continue
-                i, ln = max(enumerate(self.pools[nm]), key=lambda t: t[1].pool.free_frames())
-                b = min(pend, self.max_batch, ln.pool.free_frames())
+                lanes_nm = self.pools[nm]
+                if len(lanes_nm) == 1:
+                    i, ln = 0, lanes_nm[0]
+                    free = ln.pool.free_frames()
+                else:
+                    i, ln = max(enumerate(lanes_nm), key=lambda t: t[1].pool.free_frames())
+                    free = ln.pool.free_frames()
+                b = min(pend, self.max_batch, free)
                 if b <= 0:
                     continue
                 lo, hi = sub[nm], sub[nm] + b
                 with torch.cuda.stream(ln.stream):
                     ln.y[:b].copy_(y_pinned[nm][lo:hi], non_blocking=True)
-                    ln.pool.submit(ln.y[:b], dev[nm]["cw"][lo:hi], dev[nm]["fl"][lo:hi], dev[nm]["done"][lo:hi],
-                                   stream=ln.stream)
-                    ev = torch.cuda.Event(enable_timing=True)
-                    ev.record(ln.stream)
+                ln.pool.submit(ln.y[:b], dev[nm]["cw"][lo:hi], dev[nm]["fl"][lo:hi], dev[nm]["done"][lo:hi],
+                               stream=ln.stream)
+                ev = ev_free.pop() if ev_free else torch.cuda.Event(enable_timing=True)
+                ev.record(ln.stream)
                 ln.sub_ev.append(ev)
                 lane_of[nm][lo:hi] = i
                 sub[nm] = hi
@@ -215,10 +223,9 @@ class Server:
                 evs = ln.step_ev
                 if len(evs) >= self.steps_ahead and not evs[-self.steps_ahead].query():
                     continue
-                with torch.cuda.stream(ln.stream):
-                    ln.pool.step(stream=ln.stream)
-                    ev = torch.cuda.Event(enable_timing=True)
-                    ev.record(ln.stream)
+                ln.pool.step(stream=ln.stream)
+                ev = ev_free.pop() if ev_free else torch.cuda.Event(enable_timing=True)
+                ev.record(ln.stream)
                 evs.append(ev)
         torch.cuda.synchronize()
         lat, cws, fls, steps, rows, subs = {}, {}, {}, {}, {}, {}
