@@ -111,11 +111,10 @@ struct CodeDev {
     // Every pattern is a coset a + V of a linear subspace V of F_2^m (a position
     // j read as the m-bit vector of its binary digits) whose orthogonal
     // complement has dimension flat_kd (1 or 2); one entry per complement D:
-    // flat_off[e] = byte offsets in the flats kernel's shared-memory image of
-    // the Walsh-Hadamard coefficients Z(w1) | Z(w2) << 16, Z(w1 ^ w2), for a
-    // basis w1, w2 of D; flat_idx[4 e + c1 + 2 c2] = the pattern that is the
-    // coset with w1.a = c1, w2.a = c2 (every coset of every entry is present).
-    uint2 *flat_off = nullptr;
+    // flat_w[e] = w1 | w2 << 8 | (w1 ^ w2) << 16 for a basis w1, w2 of D (w2 = 0
+    // when kd = 1); flat_idx[4 e + c1 + 2 c2] = the pattern that is the coset
+    // with w1.a = c1, w2.a = c2 (every coset of every entry is present).
+    uint32_t *flat_w = nullptr;
     int32_t *flat_idx = nullptr;
     int n_flat = 0;
     int flat_kd = 0;
@@ -209,7 +208,6 @@ inline int osd_candidates(int k, int order) {
 cudaError_t launch_osd(const CodeDev &c, const OsdArgs &a, cudaStream_t s);
 cudaError_t launch_score_fp32(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
 // Exact scoring of a flat pattern set by Walsh-Hadamard coefficients (score_flats.cu)
-constexpr int kFlatsThreads = 128;  // threads per CTA of the flats kernel (fixes the shared-memory offsets)
 cudaError_t launch_score_flats(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
 cudaError_t launch_score_tc(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
 // y (B x n) -> bf16 hi / lo words and ||y||_1 per frame, for direct-mode tensor-core scoring

@@ -175,7 +175,7 @@ static void free_code_device(CodeDev &d) {
     cudaFree(d.pat_bits);
     cudaFree(d.pat_supp);
     cudaFree(d.pat_tiles);
-    cudaFree(d.flat_off);
+    cudaFree(d.flat_w);
     cudaFree(d.flat_idx);
     cudaFree(d.crc_masks);
     cudaFree(d.gen_rows);
@@ -184,7 +184,7 @@ static void free_code_device(CodeDev &d) {
     d.pat_bits = nullptr;
     d.pat_supp = nullptr;
     d.pat_tiles = nullptr;
-    d.flat_off = nullptr;
+    d.flat_w = nullptr;
     d.flat_idx = nullptr;
     d.crc_masks = nullptr;
     d.gen_rows = nullptr;
@@ -195,10 +195,10 @@ static void free_code_device(CodeDev &d) {
 // Flat structure of a pattern set for MPWSD_SCORE_FLATS. Positions j are read
 // as m-bit vectors (the binary digits of j, the coordinates of the Arikan
 // form). Returns the complement dimension kd (1 or 2) and fills the entries
-// (see CodeDev::flat_off / flat_idx) when every pattern is a coset a + V of a
+// (see CodeDev::flat_w / flat_idx) when every pattern is a coset a + V of a
 // linear subspace V, all of one dimension m - kd, and every coset of every V
 // that occurs is in the set; returns 0 otherwise.
-static int flats_table(int n, int m, const uint64_t *patterns, int64_t P, int W, std::vector<uint2> &off,
+static int flats_table(int n, int m, const uint64_t *patterns, int64_t P, int W, std::vector<uint32_t> &off,
                        std::vector<int32_t> &idx) {
     off.clear();
     idx.clear();
@@ -255,10 +255,9 @@ static int flats_table(int n, int m, const uint64_t *patterns, int64_t P, int W,
     for (size_t e = 0; e < basis.size(); ++e)  // every coset present
         for (int c = 0; c < (1 << kd); ++c)
             if (idx[e * 4 + (size_t)c] < 0) return 0;
-    const unsigned stride = (unsigned)kFlatsThreads * 4u;  // bytes between Z(w) and Z(w + 1) of one thread
     for (auto &b : basis) {
         const unsigned w1 = (unsigned)b[0], w2 = (unsigned)b[1];
-        off.push_back(make_uint2(w1 * stride | ((w2 * stride) << 16), (w1 ^ w2) * stride));
+        off.push_back(w1 | (w2 << 8) | ((w1 ^ w2) << 16));
     }
     return kd;
 }
@@ -448,17 +447,17 @@ extern "C" int mpwsd_load_code(int n, const uint8_t *G, const uint8_t *frozen, i
         }
     }
     // flat structure of the pattern set (MPWSD_SCORE_FLATS)
-    std::vector<uint2> flat_off;
+    std::vector<uint32_t> flat_w;
     std::vector<int32_t> flat_idx;
-    d.flat_kd = flats_table(n, m, patterns, n_patterns, W, flat_off, flat_idx);
-    d.n_flat = d.flat_kd ? (int)flat_off.size() : 0;
+    d.flat_kd = flats_table(n, m, patterns, n_patterns, W, flat_w, flat_idx);
+    d.n_flat = d.flat_kd ? (int)flat_w.size() : 0;
     // device images
     struct Up {
         void **dst;
         const void *src;
         size_t bytes;
     } ups[] = {
-        {(void **)&d.flat_off, flat_off.data(), flat_off.size() * sizeof(uint2)},
+        {(void **)&d.flat_w, flat_w.data(), flat_w.size() * 4},
         {(void **)&d.flat_idx, flat_idx.data(), flat_idx.size() * 4},
         {(void **)&d.pat_bits, patterns, (size_t)n_patterns * W * 8},
         {(void **)&d.pat_supp, supp.data(), supp.size() * 4},

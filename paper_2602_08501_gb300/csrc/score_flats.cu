@@ -15,13 +15,13 @@
 // of at most 32 terms below 2^23, and intermediate wrap-around cancels in
 // two's-complement arithmetic.
 //
-// Mapping: one thread per row. The row's z goes through the transform in
-// registers; the coefficients are stored to shared memory with the thread
-// index innermost (conflict-free), and the loop over the complements reads
-// them at the byte offsets stored in the code's table, which each CTA first
-// copies to shared memory, unpacked to one 32-bit offset per coefficient (16
-// bytes an entry, so the loop spends no instruction on unpacking; every lane
-// reads the same entry, a broadcast). Z(0) is common to the 2^kd sums of a complement and the smallest of
+// Mapping: one thread per row, FT threads per CTA. The row's z goes through
+// the transform in registers; the coefficients are stored to shared memory
+// with the thread index innermost (conflict-free), and the loop over the
+// complements reads them at byte offsets that each CTA first derives from the
+// code's table (w1, w2, w1 ^ w2 of each complement) into shared memory, one
+// 32-bit offset per coefficient (16 bytes an entry, so the loop spends no
+// instruction on unpacking; every lane reads the same entry, a broadcast). Z(0) is common to the 2^kd sums of a complement and the smallest of
 // them is Z(0) + min(Z(w1) - |Z(w2) + Z(w1^w2)|, -Z(w1) - |Z(w2) - Z(w1^w2)|)
 // (Z(0) - |Z(w1)| for kd = 1), so pass 1 takes that minimum relative to Z(0),
 // keeping the smallest value, the first complement that reaches it and
@@ -37,7 +37,8 @@
 namespace mpwsd {
 namespace {
 
-constexpr int kFT = kFlatsThreads;
+// threads per CTA for n = 32, 64, 128 (256 for n = 64 measured the same as 128)
+constexpr int kFlatsThreads32 = 128, kFlatsThreads64 = 128, kFlatsThreads128 = 128;
 
 template <int KD>
 __device__ __forceinline__ void coset_sums(int z0, int z1, int z2, int z3, int &s0, int &s1, int &s2, int &s3) {
@@ -54,7 +55,7 @@ __device__ __forceinline__ void coset_sums(int z0, int z1, int z2, int z3, int &
     }
 }
 
-template <int N, int KD>
+template <int N, int KD, int kFT>
 __global__ void __launch_bounds__(kFT) score_flats_kernel(const ScoreArgs a, const CodeDev c) {
     constexpr int W = (N + 63) / 64;
     extern __shared__ int zs[];  // Z(w) of thread t at zs[w * kFT + t]
@@ -63,9 +64,10 @@ __global__ void __launch_bounds__(kFT) score_flats_kernel(const ScoreArgs a, con
     const char *zb = reinterpret_cast<const char *>(zs + tid);
     const int ne = c.n_flat;
     uint4 *tab = reinterpret_cast<uint4 *>(zs + N * kFT);  // the complement table, after the coefficients
+    constexpr unsigned stride = (unsigned)kFT * 4u;  // bytes between Z(w) and Z(w + 1) of one thread
     for (int e = tid; e < ne; e += kFT) {
-        const uint2 q = c.flat_off[e];
-        tab[e] = make_uint4(q.x & 0xffffu, q.x >> 16, q.y, 0u);
+        const uint32_t q = c.flat_w[e];
+        tab[e] = make_uint4((q & 0xffu) * stride, ((q >> 8) & 0xffu) * stride, ((q >> 16) & 0xffu) * stride, 0u);
     }
     __syncthreads();
     for (int r = blockIdx.x * kFT + tid; r < nrows; r += gridDim.x * kFT) {
@@ -147,18 +149,18 @@ __global__ void __launch_bounds__(kFT) score_flats_kernel(const ScoreArgs a, con
     }
 }
 
-template <int N, int KD>
+template <int N, int KD, int kFT>
 cudaError_t launch_nk(const CodeDev &c, const ScoreArgs &a, cudaStream_t s) {
     const int smem = N * kFT * 4 + c.n_flat * 16;
-    cudaError_t e = cudaFuncSetAttribute(score_flats_kernel<N, KD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(score_flats_kernel<N, KD, kFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;  // CTAs that fit on an SM beside each other (registers, shared memory)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, score_flats_kernel<N, KD>, kFT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, score_flats_kernel<N, KD, kFT>, kFT, smem);
     if (e != cudaSuccess) return e;
     int64_t grid = (int64_t)c.num_sms * std::max(per_sm, 1);
     if (!a.n_rows_dev) grid = std::min<int64_t>(grid, (a.n_rows + kFT - 1) / kFT);
     if (grid <= 0) return cudaSuccess;
-    score_flats_kernel<N, KD><<<(unsigned)grid, kFT, smem, s>>>(a, c);
+    score_flats_kernel<N, KD, kFT><<<(unsigned)grid, kFT, smem, s>>>(a, c);
     return cudaGetLastError();
 }
 
@@ -168,9 +170,11 @@ cudaError_t launch_score_flats(const CodeDev &c, const ScoreArgs &a, cudaStream_
     static_assert(kTopK == 4, "one float4 / int4 list per row");
     if (c.n_flat == 0) return cudaErrorInvalidValue;
     const bool k2 = c.flat_kd == 2;
-    if (c.n == 32) return k2 ? launch_nk<32, 2>(c, a, s) : launch_nk<32, 1>(c, a, s);
-    if (c.n == 64) return k2 ? launch_nk<64, 2>(c, a, s) : launch_nk<64, 1>(c, a, s);
-    if (c.n == 128) return k2 ? launch_nk<128, 2>(c, a, s) : launch_nk<128, 1>(c, a, s);
+    // threads per CTA: shared memory holds n coefficients per thread plus the table
+    if (c.n == 32) return k2 ? launch_nk<32, 2, kFlatsThreads32>(c, a, s) : launch_nk<32, 1, kFlatsThreads32>(c, a, s);
+    if (c.n == 64) return k2 ? launch_nk<64, 2, kFlatsThreads64>(c, a, s) : launch_nk<64, 1, kFlatsThreads64>(c, a, s);
+    if (c.n == 128)
+        return k2 ? launch_nk<128, 2, kFlatsThreads128>(c, a, s) : launch_nk<128, 1, kFlatsThreads128>(c, a, s);
     return cudaErrorNotSupported;
 }
 
