@@ -586,7 +586,11 @@ def run_ours(args, wl_cfg):
             wq = math.ceil(wmax / 4)
             cand = stats["rerank_candidates"] / rows if rows else 0.0
             hopf = stats["hops"] / rows if rows else 0.0
-            bpr = 36 + 8 * W + 12 + (4 * n + 8) / L + cand * 4 * wq + hopf * (8 * W + 16)
+            if args.mode == "bf16x2":
+                # rows resolved from tensor-core groups carry their exact sum: no supports, no y
+                bpr = 36 + 8 * W + 12 + hopf * (8 * W + 16)
+            else:
+                bpr = 36 + 8 * W + 12 + (4 * n + 8) / L + cand * 4 * wq + hopf * (8 * W + 16)
             ach = bpr * rows / launches / per_launch_s / 1e9
             src = src_hash("paper_2602_08501_gb300/csrc/traj.cu", "paper_2602_08501_gb300/csrc/common.cuh",
                            "paper_2602_08501_gb300/csrc/internal.h")
@@ -595,11 +599,21 @@ def run_ours(args, wl_cfg):
             return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": ach / peaks["hbm_gbs"], "traffic": tr, "traffic_source": traffic_note, "kernel": "hop",
                     "peak_kind": f"HBM copy, {peaks['source']}", "bytes_per_row": bpr}
+        if kname == "resolve":
+            # bytes a row needs: its list in and out (36 + 32), row / slot / frame ids, centre, 1/L of
+            # its frame's y row, and the supports of one group of kGroupCols = 8 patterns
+            rows = evals / P if P else 0.0
+            wq = math.ceil(wmax / 4)
+            bpr = 36 + 32 + 12 + 8 * W + (4 * n + 8) / L + 8 * 4 * wq
+            ach = bpr * rows / launches / per_launch_s / 1e9
+            return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "resolve",
+                    "peak_kind": f"HBM copy, {peaks['source']}", "bytes_per_row": bpr}
         return {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
                 "kernel": kname}
 
     roof = roofline_for(dominant)
-    others = [roofline_for(k) for k in ("scl", "osd", "score_tc", "score_fp32", "score_flats", "hop")
+    others = [roofline_for(k) for k in ("scl", "osd", "score_tc", "resolve", "score_fp32", "score_flats", "hop")
               if k in kinds and k != dominant]
 
     line = {

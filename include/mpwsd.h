@@ -65,7 +65,9 @@ extern "C" {
 #define MPWSD_TOPK 4            /* candidates kept per trajectory by the scoring kernels */
 
 /* ---- options ------------------------------------------------------------ */
-#define MPWSD_SCORE_BF16X2 0    /* tcgen05 tensor cores, y split into bf16 hi + lo, FP32 accumulate */
+#define MPWSD_SCORE_BF16X2 0    /* tcgen05 tensor cores, y split into bf16 hi + lo, FP32 accumulate; the
+                                   kernel keeps candidate groups of 8 consecutive patterns, and a second
+                                   kernel scores their patterns exactly (integers on the 2^-19 grid) */
 #define MPWSD_SCORE_FP32 1      /* FP32 CUDA cores, sparse gather-add over each pattern's support */
 #define MPWSD_SCORE_FLATS 2     /* exact integer scores from Walsh-Hadamard coefficients, for pattern sets made
                                    of all cosets of subspaces whose complements have dimension 1 or 2 (the
@@ -377,6 +379,12 @@ MPWSD_API int mpwsd_osd_list(mpwsd_code *code, const float *y_dev, int64_t B, in
  * the patterns with S~ <= min S~ + 2 eps, i.e. every pattern that can be the
  * exact minimum unless MPWSD_TOPK of them fill the list (then the list's last
  * value is within 2 eps of its first, which the caller reads as "rescan").
+ * BF16X2 and FLATS go further and return the exact argmin: one entry, the
+ * pattern of smallest exact S (lowest index among equal ones) with that S.
+ * BF16X2 keeps groups of 8 consecutive patterns and scores the patterns of the
+ * groups within 2 eps exactly; when four groups lie within 2 eps (a full list,
+ * "rescan"), each entry is a group's smallest S~ with the group's pattern of
+ * smallest exact S.
  *
  *   y_dev       device, B x n FP32.       frame_dev  device, M int32 in [0, B).
  *   cw_dev      device, M x W uint64.     M          rows, >= 0.
@@ -401,7 +409,8 @@ MPWSD_API int mpwsd_sync(mpwsd_code *code, void *stream);
 #define MPWSD_KERNEL_FINAL 5      /* per-frame argmin ED + flags */
 #define MPWSD_KERNEL_OSD 6        /* stage 1 by OSD(order) + CRC + compaction */
 #define MPWSD_KERNEL_SCORE_FLATS 7 /* scoring, exact Walsh-Hadamard coset sums (MPWSD_SCORE_FLATS) */
-#define MPWSD_KERNEL_KINDS 8
+#define MPWSD_KERNEL_RESOLVE 8    /* exact argmin inside the candidate groups of the tcgen05 scoring */
+#define MPWSD_KERNEL_KINDS 9
 
 typedef struct mpwsd_kernel_time {
     int64_t launches; /* kernels of this class launched while profiling */

@@ -13,6 +13,13 @@ constexpr int kTopK = MPWSD_TOPK;
 // for n = 64 (one 128 x 256 x 16 MMA chain per row block), 128 for n = 128
 // (shared memory holds fewer, twice-as-deep tiles).
 __host__ __device__ constexpr int tc_patterns_per_tile(int n) { return n == 64 ? 256 : 128; }
+// The tensor-core epilogue keeps candidate groups of kGroupCols consecutive
+// patterns (group g: patterns 8g .. 8g + 7); resolve_groups_kernel scores their
+// patterns exactly and leaves the argmin pattern.
+constexpr int kGroupCols = 8;
+// List slot 1 of a resolved row: index kExactTag, value = the exact integer
+// sum (2^-19 grid units) of slot 0's pattern, bit-cast to float.
+constexpr int kExactTag = -2;
 constexpr int kGridShift = 19;            // y is read on the 2^-19 grid
 constexpr int kGridMax = (1 << 23) - 1;   // |round(y 2^19)| <= 2^23 - 1
 // Margin of the near-tie re-rank: every approximate score is within
@@ -191,6 +198,9 @@ struct ScoreArgs {
     int *split_idx;
     int *unit_done;
     int split_items;  // target work items of the split (<= kSplitItemsPerSm / 2 x SMs)
+    // decode: the group resolution also leaves the exact integer sum of the row's
+    // argmin in list slot 1 (tagged kExactTag) so the re-rank need not recompute it
+    bool exact_tag;
 };
 
 // Launchers (return cudaError_t of the launch).
@@ -210,6 +220,8 @@ cudaError_t launch_score_fp32(const CodeDev &c, const ScoreArgs &a, cudaStream_t
 // Exact scoring of a flat pattern set by Walsh-Hadamard coefficients (score_flats.cu)
 cudaError_t launch_score_flats(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
 cudaError_t launch_score_tc(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
+// exact argmin pattern of each row from the candidate groups launch_score_tc keeps
+cudaError_t launch_resolve_groups(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
 // y (B x n) -> bf16 hi / lo words and ||y||_1 per frame, for direct-mode tensor-core scoring
 cudaError_t launch_split_prep(const CodeDev &c, const float *y, int64_t B, uint32_t *yhl, float *l1, cudaStream_t s);
 bool score_tc_supported(const CodeDev &c);

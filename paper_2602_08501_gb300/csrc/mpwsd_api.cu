@@ -643,7 +643,10 @@ static cudaError_t launch_score(mpwsd_code *code, int mode, const ScoreArgs &a, 
         return timed_launch(code, MPWSD_KERNEL_SCORE_FP32, s, [&] { return launch_score_fp32(code->d, a, s); });
     if (mode == MPWSD_SCORE_FLATS)
         return timed_launch(code, MPWSD_KERNEL_SCORE_FLATS, s, [&] { return launch_score_flats(code->d, a, s); });
-    return timed_launch(code, MPWSD_KERNEL_SCORE_TC, s, [&] { return launch_score_tc(code->d, a, s); });
+    // tensor cores keep candidate groups; their exact argmin follows in its own kernel
+    cudaError_t e = timed_launch(code, MPWSD_KERNEL_SCORE_TC, s, [&] { return launch_score_tc(code->d, a, s); });
+    if (e != cudaSuccess) return e;
+    return timed_launch(code, MPWSD_KERNEL_RESOLVE, s, [&] { return launch_resolve_groups(code->d, a, s); });
 }
 
 // Host buffers of mpwsd_decode_host: y is copied in chunk by chunk on the copy
@@ -736,6 +739,7 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
         a.split_idx = ws.split_idx;
         a.unit_done = ws.unit_done;
         a.split_items = d.split_items;
+        a.exact_tag = true;
         e = launch_score(code, o.score_mode, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "scoring launch");
         e = timed_launch(code, MPWSD_KERNEL_HOP, s, [&] { return launch_hop(d, ws, it, L, y_dev, s); });
@@ -758,6 +762,20 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
         if (e != cudaSuccess) return cuda_fail(e, "copying the results to the host");
     }
     return MPWSD_OK;
+}
+
+// Kernel nodes of a captured graph (each replay launches that many kernels).
+static int graph_kernel_nodes(cudaGraph_t graph) {
+    size_t nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nodes);
+    std::vector<cudaGraphNode_t> list(nodes);
+    if (nodes) cudaGraphGetNodes(graph, list.data(), &nodes);
+    int kernels = 0;
+    for (auto nd : list) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+    }
+    return kernels;
 }
 
 // Decode through a cached CUDA graph of the launch sequence: on a miss the
@@ -793,15 +811,7 @@ static int decode_graph(mpwsd_code *code, Workspace &ws, const float *y_dev, int
         return st;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    size_t nodes = 0;
-    cudaGraphGetNodes(graph, nullptr, &nodes);
-    std::vector<cudaGraphNode_t> list(nodes);
-    if (nodes) cudaGraphGetNodes(graph, list.data(), &nodes);
-    int kernels = 0;
-    for (auto nd : list) {
-        cudaGraphNodeType ty;
-        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
-    }
+    const int kernels = graph_kernel_nodes(graph);
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -1300,6 +1310,7 @@ static int pool_step_launches(mpwsd_pool *p, cudaStream_t s) {
     a.split_idx = ws.split_idx;
     a.unit_done = ws.unit_done;
     a.split_items = d.split_items;
+    a.exact_tag = true;
     cudaError_t e = launch_score(code, p->o.score_mode, a, s);
     if (e != cudaSuccess) return cuda_fail(e, "scoring launch");
     const float *y = ws.pool.slot_y;
@@ -1468,10 +1479,10 @@ extern "C" int mpwsd_pool_step(mpwsd_pool *p, void *stream) {
                 return st;
             }
             if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            p->graph_kernels = graph_kernel_nodes(graph);
             e = cudaGraphInstantiate(&p->graph, graph, 0);
             cudaGraphDestroy(graph);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-            p->graph_kernels = 6;
         }
         cudaError_t e = cudaGraphLaunch(p->graph, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");

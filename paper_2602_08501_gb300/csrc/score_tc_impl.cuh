@@ -6,10 +6,14 @@
 // S = Z P^T, a dense contraction. z is split as z = hi + lo with hi, lo
 // bf16 (|z - hi - lo| <= 2^-16 |z|), so S ~= [Z_hi | Z_lo] [P | P]^T is two
 // bf16 MMAs per K step into one FP32 accumulator; P is exact in bf16. The
-// epilogue keeps each row's candidates for the exact argmin (at most four, the
-// ones within the re-rank margin of the row's minimum), so the score matrix
-// never reaches HBM; the FP64 re-rank and the hop follow in their own kernel,
-// where a grid of short rows hides their memory latency.
+// epilogue keeps each row's candidate groups for the exact argmin (at most
+// four groups of 8 consecutive patterns, those whose smallest approximate
+// score is within the re-rank margin of the row's minimum), so the score
+// matrix never reaches HBM. Locating the column inside a group would cost the
+// epilogue, which paces this kernel for n = 64, more than the MMAs; instead
+// resolve_groups_kernel scores the patterns of the kept groups exactly (integer
+// sums on the 2^-19 grid) and leaves the single exact argmin, and the hop
+// follows in its own kernel, where a grid of short rows hides memory latency.
 //
 // Kernel shape (sm_103a): persistent, one CTA per SM, units of 256 rows (two
 // 128-row blocks that share every pattern tile, halving the L2 traffic of the
@@ -20,7 +24,7 @@
 //               streamed through a two-stage smem ring;
 //   warp 1      TMEM allocator and single-thread MMA issuer
 //               (tcgen05.mma.cta_group::1.kind::f16, M = 128, K = 16);
-//   A builders  warps 2-3 (and 12-13 for n = 64): gather frame and centre of
+//   A builders  warps 2-3 (and 12-13 in the four-builder shapes): gather frame and centre of
 //               their rows, then y rows 16 at a time, form z, split to bf16
 //               hi / lo, write the swizzled A tiles;
 //   warps 4-11  epilogue: warp 4 + 4h + q reads TMEM lane quadrant q (one row
@@ -30,8 +34,9 @@
 //               accumulator released once its last columns are in
 //               registers); takes minima of 8-column groups with
 //               three-input mins, and only groups that beat the row's
-//               admission threshold enter its running top-K; at the end of a
-//               unit the two halves of each row's list meet in shared memory.
+//               admission threshold enter its running top-K (as group
+//               indices); at the end of a unit the two halves of each row's
+//               list meet in shared memory.
 // MMAs into one accumulator serialise (one chain of 128 x 128 x 16 MMAs runs
 // at about 60 % of the tensor rate, 128 x 256 x 16 at the full rate), so the
 // issue order is chosen per n. n = 64: per tile, row block 0 then row block 1,
@@ -138,9 +143,10 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 // Bounded wait for the phase of parity `parity`; false on abort or timeout.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int *abort_flag,
-                                       uint64_t limit_ns) {
-    if (mbar_try(bar, parity)) return true;
+// The first try is inline (usually the phase is complete, and a call would
+// cost the epilogue register moves around it); the sleeping loop is a call.
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, const volatile int *abort_flag,
+                                            uint64_t limit_ns) {
     const uint64_t t0 = global_ns();
     for (uint32_t i = 1; i < (1u << 30); ++i) {
         if (mbar_try_sleep(bar, parity)) return true;
@@ -148,6 +154,10 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const vola
         if (global_ns() - t0 > limit_ns) return false;
     }
     return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int *abort_flag,
+                                          uint64_t limit_ns) {
+    return mbar_try(bar, parity) || mbar_wait_slow(bar, parity, abort_flag, limit_ns);
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
@@ -244,69 +254,31 @@ __device__ __forceinline__ float admit_thr(const float (&tv)[kTopK], float eps2)
     return fminf(tv[kTopK - 1], __fadd_ru(tv[0], eps2));
 }
 
-// Move every value of group G8 below the admission threshold into the running
-// list: take the group minimum, insert it (its lowest position on ties), blank
-// it, repeat. Usually zero or one round.
-template <int G8, int CW>
-__device__ __forceinline__ void drain_group(uint32_t (&v)[CW], float gm, float (&tv)[kTopK], int (&ti)[kTopK],
-                                            float &thr, float eps2, int cbase) {
-    while (gm < thr) {
-        int pos = 7;
-#pragma unroll
-        for (int e = 6; e >= 0; --e) pos = (__uint_as_float(v[8 * G8 + e]) == gm) ? e : pos;
-        topk_insert<kTopK>(tv, ti, gm, cbase + 8 * G8 + pos);
-        thr = admit_thr(tv, eps2);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[8 * G8 + e] = (e == pos) ? __float_as_uint(CUDART_INF_F) : v[8 * G8 + e];
-        gm = min8<G8, CW>(v);
-    }
-}
-
-template <int G8, int CW>
-__device__ __forceinline__ void scan_groups(uint32_t (&v)[CW], const float (&gm)[CW / 8], float (&tv)[kTopK],
-                                            int (&ti)[kTopK], float &thr, float eps2, int cbase) {
-    if constexpr (G8 < CW / 8) {
-        if (gm[G8] < thr) drain_group<G8, CW>(v, gm[G8], tv, ti, thr, eps2, cbase);
-        scan_groups<G8 + 1, CW>(v, gm, tv, ti, thr, eps2, cbase);
-    }
-}
-
 // Admission of one CW-column chunk whose minimum m beats the row's threshold.
 // Once m is in the list nothing at or above t1 = min(thr, m + 2 eps) can
-// enter, so the chunk matters only through its columns below t1. Column e
-// lies in row group e / 8 (minima gm) and in strided set e % 8 (minima sm);
-// if exactly one row group and one strided set reach below t1, exactly one
-// column does: m itself, at 8 g + b, and it is inserted without a search.
-// Otherwise (a near-tie inside the chunk, or eps = 0) the groups are drained
-// one by one. Every lane runs the same instructions on the fast path, so a
-// warp pays for one admission per chunk however many of its rows have one.
+// enter, so the chunk matters only through its 8-column groups whose minimum
+// is below t1; each enters as (group minimum, group index). Usually that is
+// the one group holding m, inserted without a search; two or more (a near tie
+// across groups of the chunk) are inserted one by one in group order.
 template <int CW>
-__device__ __forceinline__ void admit_chunk(uint32_t (&v)[CW], const float (&gm)[CW / 8], float m, float (&tv)[kTopK],
-                                            int (&ti)[kTopK], float &thr, float eps2, int cbase) {
+__device__ __forceinline__ void admit_chunk(const float (&gm)[CW / 8], float m, float (&tv)[kTopK], int (&ti)[kTopK],
+                                            float &thr, float eps2, int gbase) {
     static_assert(CW == 32 || CW == 64, "chunks of 32 or 64 columns");
     const float t1 = fminf(thr, __fadd_ru(m, eps2));
-    int na = 0, nb = 0, ga = 0, gb = 0;
+    unsigned below = 0u;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        float sm;  // minimum of the strided set b, b + 8, b + 16, ...
-        if constexpr (CW == 64)
-            sm = fmin3(fmin3(__uint_as_float(v[b]), __uint_as_float(v[b + 8]), __uint_as_float(v[b + 16])),
-                       fmin3(__uint_as_float(v[b + 24]), __uint_as_float(v[b + 32]), __uint_as_float(v[b + 40])),
-                       fminf(__uint_as_float(v[b + 48]), __uint_as_float(v[b + 56])));
-        else
-            sm = fminf(fmin3(__uint_as_float(v[b]), __uint_as_float(v[b + 8]), __uint_as_float(v[b + 16])),
-                       __uint_as_float(v[b + 24]));
-        const bool pa = b < CW / 8 && gm[b < CW / 8 ? b : 0] < t1, pb = sm < t1;
-        na += pa;
-        ga += pa ? b : 0;
-        nb += pb;
-        gb += pb ? b : 0;
-    }
-    if (na == 1 && nb == 1) {
-        topk_insert<kTopK>(tv, ti, m, cbase + 8 * ga + gb);
+    for (int g = 0; g < CW / 8; ++g) below |= gm[g] < t1 ? (1u << g) : 0u;
+    if (__popc(below) == 1) {
+        topk_insert<kTopK>(tv, ti, m, gbase + __ffs(below) - 1);
         thr = admit_thr(tv, eps2);
     } else {
-        scan_groups<0, CW>(v, gm, tv, ti, thr, eps2, cbase);
+#pragma unroll
+        for (int g = 0; g < CW / 8; ++g) {
+            if (gm[g] < thr) {
+                topk_insert<kTopK>(tv, ti, gm[g], gbase + g);
+                thr = admit_thr(tv, eps2);
+            }
+        }
     }
 }
 
@@ -320,7 +292,8 @@ __device__ __forceinline__ void group_mins(const uint32_t (&v)[CW], float (&gm)[
 
 // One CW-column chunk of a row's scores into its running list: group minima,
 // the chunk minimum, and an admission when it beats the row's threshold.
-// Columns at or past P (the last tile's padding) count as +inf.
+// Columns at or past P (the last tile's padding) count as +inf. cbase is the
+// chunk's first column, a multiple of 8 (list entries are group indices).
 template <int CW>
 __device__ __forceinline__ void epi_chunk(uint32_t (&v)[CW], int cbase, int P, bool full, float (&tv)[kTopK],
                                           int (&ti)[kTopK], float &thr, float eps2) {
@@ -336,7 +309,7 @@ __device__ __forceinline__ void epi_chunk(uint32_t (&v)[CW], int cbase, int P, b
         m = fmin3(fmin3(gm[0], gm[1], gm[2]), fmin3(gm[3], gm[4], gm[5]), fminf(gm[6], gm[7]));
     else
         m = fminf(fmin3(gm[0], gm[1], gm[2]), gm[3]);
-    if (m < thr) admit_chunk<CW>(v, gm, m, tv, ti, thr, eps2, cbase);
+    if (m < thr) admit_chunk<CW>(gm, m, tv, ti, thr, eps2, cbase / kGroupCols);
 }
 
 __device__ __forceinline__ uint32_t bf16_bits(__nv_bfloat16 h) { return (uint32_t)__bfloat16_as_ushort(h); }
@@ -770,10 +743,10 @@ __global__ void __launch_bounds__(TcCfg<N, BN_, BLD, BST>::THREADS, 1) score_tc_
                     }
                     tc_fence_after();
                 }
-                // one copy of the chunk code: the current row block's list is always
-                // entry 0 (the two swap after each row block)
-                static_assert(RB == 2, "two row blocks swap places");
-#pragma unroll 1
+                // both row blocks' code unrolled, each on its own list registers (one
+                // copy with the lists swapped after each row block measured 4-6 % slower:
+                // the swaps cost more moves than the second copy costs fetch)
+#pragma unroll
                 for (int rbx = 0; rbx < RB; ++rbx) {
                     if constexpr (C::SEQ) {
                         bool w = mbar_wait(smem_u32(&sh.acc_full[rbx]), (uint32_t)gacc & 1u, abort_flag, c.wait_limit_ns);
@@ -791,7 +764,7 @@ __global__ void __launch_bounds__(TcCfg<N, BN_, BLD, BST>::THREADS, 1) score_tc_
                     {
                         const unsigned long long pb = best[1 - h];
                         if ((int)(pb >> 32) == item)
-                            thr[0] = fminf(thr[0], __fadd_ru(__uint_as_float((uint32_t)pb), eps2[0]));
+                            thr[rbx] = fminf(thr[rbx], __fadd_ru(__uint_as_float((uint32_t)pb), eps2[rbx]));
                     }
                     const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + col;
                     const int cb0 = j * C::BN + h * HALF;
@@ -805,7 +778,7 @@ __global__ void __launch_bounds__(TcCfg<N, BN_, BLD, BST>::THREADS, 1) score_tc_
                             uint32_t v[64];
                             __syncwarp();
                             tmem_ld64(tbase + (uint32_t)(cc * 64), v);
-                            epi_chunk<64>(v, cb0 + cc * 64, P, full, tv[0], ti[0], thr[0], eps2[0]);
+                            epi_chunk<64>(v, cb0 + cc * 64, P, full, tv[rbx], ti[rbx], thr[rbx], eps2[rbx]);
                         }
                         tc_fence_before();
                         mbar_arrive(smem_u32(&sh.acc_empty[rbx]));
@@ -823,7 +796,7 @@ __global__ void __launch_bounds__(TcCfg<N, BN_, BLD, BST>::THREADS, 1) score_tc_
                         for (int sl = 0; sl < NS; sl += 2) {
                             __syncwarp();
                             tmem_ld32(tbase + (uint32_t)((sl + 1) * 32), vb);
-                            epi_chunk<32>(va, cb0 + sl * 32, P, full, tv[0], ti[0], thr[0], eps2[0]);
+                            epi_chunk<32>(va, cb0 + sl * 32, P, full, tv[rbx], ti[rbx], thr[rbx], eps2[rbx]);
                             __syncwarp();
                             tmem_wait(vb);
                             if (sl + 2 < NS) {
@@ -833,29 +806,14 @@ __global__ void __launch_bounds__(TcCfg<N, BN_, BLD, BST>::THREADS, 1) score_tc_
                                 tc_fence_before();
                                 mbar_arrive(smem_u32(&sh.acc_empty[gacc & 1]));
                             }
-                            epi_chunk<32>(vb, cb0 + (sl + 1) * 32, P, full, tv[0], ti[0], thr[0], eps2[0]);
+                            epi_chunk<32>(vb, cb0 + (sl + 1) * 32, P, full, tv[rbx], ti[rbx], thr[rbx], eps2[rbx]);
                             if (sl + 2 < NS) {
                                 __syncwarp();
                                 tmem_wait(va);
                             }
                         }
                     }
-                    best[h] = ((unsigned long long)(uint32_t)item << 32) | __float_as_uint(tv[0][0]);
-#pragma unroll
-                    for (int e = 0; e < kTopK; ++e) {
-                        const float sv = tv[0][e];
-                        tv[0][e] = tv[1][e];
-                        tv[1][e] = sv;
-                        const int si = ti[0][e];
-                        ti[0][e] = ti[1][e];
-                        ti[1][e] = si;
-                    }
-                    const float st = thr[0];
-                    thr[0] = thr[1];
-                    thr[1] = st;
-                    const float se = eps2[0];
-                    eps2[0] = eps2[1];
-                    eps2[1] = se;
+                    best[h] = ((unsigned long long)(uint32_t)item << 32) | __float_as_uint(tv[rbx][0]);
                 }
 
             }

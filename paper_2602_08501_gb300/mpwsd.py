@@ -48,7 +48,7 @@ class _KTime(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 
-KERNEL_NAMES = ("scl", "score_tc", "score_fp32", "hop", "rescan", "final", "osd", "score_flats")
+KERNEL_NAMES = ("scl", "score_tc", "score_fp32", "hop", "rescan", "final", "osd", "score_flats", "resolve")
 
 
 class _Stats(ctypes.Structure):

@@ -117,6 +117,12 @@ def _score_case(mp, code, ocode, oracle_mod, mode, M, seed):
         # the exact minimum is kept, unless the list is full within the margin (rescan)
         best = np.flatnonzero(S == S.min())[0]
         assert best in idx[i, :cnt] or full
+        if mode == "bf16x2" and not full:
+            # the tensor-core form resolves its candidate groups exactly: the single
+            # entry is the exact argmin (lowest index on ties) with its exact score
+            assert cnt == 1 and idx[i, 0] == best, (i, idx[i], best)
+            assert abs(vals[i, 0] - S.min()) <= 1e-6 * max(1.0, abs(S.min()))
+            continue
         # every pattern left out is outside the band of the re-rank
         outside = np.setdiff1d(np.arange(P.shape[0]), idx[i, :cnt])
         if outside.size and not full:
