@@ -10,11 +10,11 @@
 // frame, 32 / LW frames per warp. The SC schedule (which f / g updates run
 // before each leaf) does not depend on the data, so it is unrolled at compile
 // time and every LLR lives in a register. At an information leaf the 2|list|
-// children are ranked by the key (metric, parent position, bit) with warp
-// shuffles; each surviving child takes a lane and copies from its parent lane
-// only the state still needed later (LLR arrays of ancestors whose right
-// subtree is pending, left-subtree codewords of ancestors whose right subtree
-// is running). Integer LLRs: inputs on the 2^-19 grid are exact int32, path
+// children are ordered by the key (metric, parent position, bit) with bitonic
+// networks across the frame's lanes; each surviving child takes a lane and
+// copies from its parent lane only the state still needed later (LLR arrays
+// of ancestors whose right subtree is pending, left-subtree codewords of
+// ancestors whose right subtree is running). Integer LLRs: inputs on the 2^-19 grid are exact int32, path
 // metrics int64, so the list equals the FP64 formulation bit for bit.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -94,7 +94,6 @@ struct PathState {
 template <class FZ>
 struct SclCtx {
     const int *ych;                // channel LLRs of this frame (shared memory)
-    unsigned long long *xchg;      // LW exchange slots of this frame (shared memory)
     int lane;                      // lane within the frame's segment
     int count;                     // current list size (uniform over the warp)
     int L;
@@ -155,20 +154,50 @@ struct LeafStep {
     unsigned bit;   // decided u of this lane's path
 };
 
+// Bitonic sort of one key per lane over the LW lanes of a frame (ascending in
+// lane order): each stage compares with the lane j apart and keeps the smaller
+// or the larger key by the lane's place in the network.
+template <int LW, class K>
+__device__ __forceinline__ K seg_sort(K x, int lane) {
+#pragma unroll
+    for (int k = 2; k <= LW; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const K o = __shfl_xor_sync(kFull, x, j, LW);
+            const bool lo = ((lane & k) == 0) == ((lane & j) == 0);
+            x = lo ? min(x, o) : max(x, o);
+        }
+    }
+    return x;
+}
+
+// The LW smallest of two ascending sequences a (in lane order) and b: against
+// b reversed, the lane-wise minima are those LW keys as a bitonic sequence,
+// which the merge half of the network puts in ascending lane order.
+template <int LW, class K>
+__device__ __forceinline__ K seg_merge_low(K a, K b, int lane) {
+    K x = min(a, __shfl_sync(kFull, b, LW - 1 - lane, LW));
+#pragma unroll
+    for (int j = LW / 2; j > 0; j >>= 1) {
+        const K o = __shfl_xor_sync(kFull, x, j, LW);
+        x = (lane & j) ? max(x, o) : min(x, o);
+    }
+    return x;
+}
+
 // The list step at an information leaf (it does not depend on which leaf, so
 // one copy of its code serves all of them): each of the |list| paths spawns
 // the children (u = HD, metric pm) and (u = 1 - HD, metric pm + |lam|); the
-// 2 |list| children are ranked by the key (metric, parent position, bit) and
-// the first min(2 |list|, L) are kept, child r going to lane r. Metrics are
-// taken relative to the frame's best path; when every relative metric of the
-// segment fits 25 bits the keys fit 32 bits (the usual case), otherwise the
-// same ranking runs on 64-bit keys.
+// 2 |list| children are ordered by the key (metric, parent position, bit) and
+// the first min(2 |list|, L) are kept, child r going to lane r. The keys are
+// distinct (parent position and bit are in them), so sorting them gives that
+// order exactly: the two children sets are sorted apart (bitonic networks
+// across the frame's lanes) and merged keeping the smallest LW, so lane r ends
+// with the r-th child. Metrics are taken relative to the frame's best path;
+// when every relative metric of the segment fits 25 bits the keys fit 32 bits
+// (the usual case), otherwise the same network runs on 64-bit keys.
 template <int LW>
-__device__ __noinline__ LeafStep list_step(int lam, long long pm, int lane, int count, int L,
-                                           unsigned long long *xchg) {
-    // the ranking loops are unrolled whole for lists of up to 8 (measured: 2 % faster
-    // at L = 8) and by 4 beyond (whole unrolling at L = 16 cost 6 % in instruction fetch)
-    constexpr int kRankUnroll = LW <= 8 ? LW : 4;
+__device__ __noinline__ LeafStep list_step(int lam, long long pm, int lane, int count, int L) {
     const unsigned hd = lam < 0 ? 1u : 0u;
     const long long a = lam < 0 ? -(long long)lam : (long long)lam;
     const bool valid = lane < count;
@@ -177,46 +206,27 @@ __device__ __noinline__ LeafStep list_step(int lam, long long pm, int lane, int 
     for (int o = LW / 2; o >= 1; o >>= 1) pmin = min(pmin, __shfl_xor_sync(kFull, pmin, o, LW));
     const long long d0 = pm - pmin;
     const bool small = !valid || d0 + a < (1LL << 25);
-    int r0 = 0, r1 = 0;
-    unsigned long long k0, k1;
+    const int nc = min(2 * count, L);
+    const bool keep = lane < nc;
+    LeafStep out;
+    out.count = nc;
     if (__all_sync(kFull, small)) {
         const uint32_t base32 = (uint32_t)lane << 1;
         const uint32_t q0 = valid ? (((uint32_t)d0 << 6) | base32 | hd) : 0xffffffffu;
         const uint32_t q1 = valid ? (((uint32_t)(d0 + a) << 6) | base32 | (hd ^ 1u)) : 0xffffffffu;
-#pragma unroll kRankUnroll
-        for (int s = 0; s < LW; ++s) {
-            const uint32_t s0 = __shfl_sync(kFull, q0, s, LW);
-            const uint32_t s1 = __shfl_sync(kFull, q1, s, LW);
-            r0 += (s0 < q0) + (s1 < q0);
-            r1 += (s0 < q1) + (s1 < q1);
-        }
-        // back to absolute 64-bit keys for the exchange
-        k0 = valid ? ((((unsigned long long)pm) << 6) | (q0 & 63u)) : ~0ull;
-        k1 = valid ? ((((unsigned long long)(pm + a)) << 6) | (q1 & 63u)) : ~0ull;
+        const uint32_t kk = seg_merge_low<LW>(seg_sort<LW>(q0, lane), seg_sort<LW>(q1, lane), lane);
+        out.par = keep ? (int)((kk >> 1) & 31u) : lane;
+        out.pm = keep ? pmin + (long long)(kk >> 6) : pm;
+        out.bit = keep ? (kk & 1u) : 0u;
     } else {
         const unsigned long long base = ((unsigned long long)lane << 1);
-        k0 = valid ? (((unsigned long long)pm << 6) | base | hd) : ~0ull;
-        k1 = valid ? (((unsigned long long)(pm + a) << 6) | base | (hd ^ 1u)) : ~0ull;
-#pragma unroll kRankUnroll
-        for (int s = 0; s < LW; ++s) {
-            const unsigned long long s0 = __shfl_sync(kFull, k0, s, LW);
-            const unsigned long long s1 = __shfl_sync(kFull, k1, s, LW);
-            r0 += (s0 < k0) + (s1 < k0);
-            r1 += (s0 < k1) + (s1 < k1);
-        }
+        const unsigned long long k0 = valid ? (((unsigned long long)pm << 6) | base | hd) : ~0ull;
+        const unsigned long long k1 = valid ? (((unsigned long long)(pm + a) << 6) | base | (hd ^ 1u)) : ~0ull;
+        const unsigned long long kk = seg_merge_low<LW>(seg_sort<LW>(k0, lane), seg_sort<LW>(k1, lane), lane);
+        out.par = keep ? (int)((kk >> 1) & 31ull) : lane;
+        out.pm = keep ? (long long)(kk >> 6) : pm;
+        out.bit = keep ? (unsigned)(kk & 1ull) : 0u;
     }
-    const int nc = min(2 * count, L);
-    if (r0 < nc) xchg[r0] = k0;
-    if (r1 < nc) xchg[r1] = k1;
-    __syncwarp();
-    const bool keep = lane < nc;
-    const unsigned long long kk = xchg[keep ? lane : 0];
-    __syncwarp();
-    LeafStep out;
-    out.par = keep ? (int)((kk >> 1) & 31ull) : lane;
-    out.pm = keep ? (long long)(kk >> 6) : pm;
-    out.count = nc;
-    out.bit = keep ? (unsigned)(kk & 1ull) : 0u;
     return out;
 }
 
@@ -227,7 +237,7 @@ __device__ __forceinline__ uint64_t info_leaf(SclCtx<FZ> &cx, PathState<N> &st) 
         // one path: the child with the smaller key is always the hard decision
         return lam < 0 ? 1u : 0u;
     } else {
-        const LeafStep o = list_step<LW>(lam, st.pm, cx.lane, cx.count, cx.L, cx.xchg);
+        const LeafStep o = list_step<LW>(lam, st.pm, cx.lane, cx.count, cx.L);
         clone_src<N, LW, I, 2>(st, o.par);
         clone_bsrc<N, LW, I, 1>(st, o.par);
         st.pm = o.pm;
@@ -326,7 +336,6 @@ __global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32) scl_kernel(const
     constexpr int WPB = SclShape<N, LW>::kWarps;
     constexpr int W = (N + 63) / 64;
     __shared__ int s_y[WPB][FPW][N];
-    __shared__ unsigned long long s_x[WPB][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int seg = lane / LW, sl = lane % LW;
     const int64_t fbase = ((int64_t)blockIdx.x * WPB + warp) * FPW;
@@ -341,7 +350,6 @@ __global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32) scl_kernel(const
 
     SclCtx<FZ> cx;
     cx.ych = s_y[warp][seg];
-    cx.xchg = &s_x[warp][seg * LW];
     cx.lane = sl;
     cx.count = 1;
     cx.L = a.L;

@@ -50,111 +50,179 @@ __global__ void __launch_bounds__(256) split_prep_kernel(const float *y, int64_t
 // may have left candidates out (the re-rank rescans it): it keeps its four
 // values, each group replaced by its pattern of smallest exact score, so every
 // value stays within eps of its pattern's exact score.
+//
+// Shared layout of a team's row: sample j at (j % PER) * 9 + j / PER (PER =
+// N / 8 samples per lane); slot 8 holds 0 and serves the support padding
+// (index N, and 255 past a pattern's words). Staging stores are then free of
+// bank conflicts: the team regions start 8 banks apart.
 constexpr int kResolveThreads = 256;
 constexpr int kResolveTeams = kResolveThreads / kGroupCols;
 
 template <int N>
+struct ResolveShape {
+    static constexpr int PER = N / kGroupCols;                  // samples per lane (8 or 16)
+    static constexpr int SH = PER == 8 ? 3 : 4;                  // log2 PER
+    static constexpr int STRIDE = PER == 8 ? 72 : 168;           // team region, = 8 (mod 32) ints
+    static_assert(STRIDE >= PER * 9 && STRIDE % 32 == 8, "team regions 8 banks apart");
+};
+
+// sum of z over 16 support indices (4 words of 4 uint8 indices)
+template <int N>
+__device__ __forceinline__ int team_sum16(const int *zb, const uint4 w) {
+    using S = ResolveShape<N>;
+    const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
+    int sum = 0;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int j = min((int)((wd[e >> 2] >> (8 * (e & 3))) & 255u), N);
+        sum += zb[(j & (S::PER - 1)) * 9 + (j >> S::SH)];
+    }
+    return sum;
+}
+
+template <int N>
+__device__ __forceinline__ uint4 supp_quad(const uint32_t *supp, int wq, int q0) {
+    if ((wq & 3) == 0) return __ldg(reinterpret_cast<const uint4 *>(supp + q0));
+    uint32_t wd[4];
+    support_words(supp, wq, q0, wd);
+    return make_uint4(wd[0], wd[1], wd[2], wd[3]);
+}
+
+template <int N>
 __global__ void __launch_bounds__(kResolveThreads) resolve_groups_kernel(const ScoreArgs a, const CodeDev c) {
     static_assert(kGroupCols == 8, "one 8-lane team per row");
-    constexpr int PER = N / kGroupCols;  // samples each lane stages (8 or 16)
+    using S = ResolveShape<N>;
+    constexpr int PER = S::PER;
     constexpr int W = (N + 63) / 64;
-    __shared__ __align__(16) int zs[kResolveTeams][N + 4];  // z of the team's row; zs[.][N] = 0 (support padding)
+    __shared__ __align__(16) int zs[kResolveTeams * S::STRIDE];
     const int nrows = a.n_rows_dev ? *a.n_rows_dev : (int)a.n_rows;
-    const int lane = threadIdx.x & 31, sub = lane & 7, tm = threadIdx.x / kGroupCols;
+    const int lane = threadIdx.x & 31, sub = lane & 7, tq = lane >> 3, tm = threadIdx.x / kGroupCols;
     const unsigned team = 0xffu << (lane & 24);
     const int wq = c.wq_max, P = (int)c.P;
-    int *z = zs[tm];
-    if (sub == 0) z[N] = 0;
-    const int64_t step = (int64_t)gridDim.x * kResolveTeams;
-    for (int64_t r = (int64_t)blockIdx.x * kResolveTeams + tm; r < nrows; r += step) {
-        const float4 v = reinterpret_cast<const float4 *>(a.topk_val)[r];
-        const int4 ix = reinterpret_cast<const int4 *>(a.topk_idx)[r];
-        const int t = a.rows ? a.rows[r] : (int)r;
-        const int slot = a.row_frame ? a.row_frame[r] : t / a.L;
-        const int fr = a.row_frame ? a.row_frame[r] : a.slot_frame[slot];
-        // the re-rank's band (same arithmetic as the hop kernel)
-        const float thr = __fadd_ru(v.x, __fmul_ru(2.0f, kEpsScale * a.l1[slot]));
-        const bool full = ix.w >= 0 && v.w <= thr;
-        const int ng = full ? 4 : (ix.x >= 0 && v.x <= thr) + (ix.y >= 0 && v.y <= thr) + (ix.z >= 0 && v.z <= thr);
-        if (ng == 0) continue;  // nothing kept (no patterns): the list stays as it is
-        // stage z: lane sub converts samples [PER sub, PER sub + PER)
-        {
-            const uint64_t cwd = a.cw[(int64_t)t * W + (W > 1 ? (sub * PER) >> 6 : 0)];
-            const float4 *yr = reinterpret_cast<const float4 *>(a.y + (int64_t)fr * N + sub * PER);
-            __syncwarp(team);  // the previous row's sums are done
-#pragma unroll
-            for (int u = 0; u < PER / 4; ++u) {
-                const float4 q = yr[u];
-                const float f[4] = {q.x, q.y, q.z, q.w};
-                int o[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int j = sub * PER + 4 * u + e;
-                    const int g = grid_q(f[e]);
-                    o[e] = ((cwd >> (j & 63)) & 1ull) ? -g : g;
-                }
-                *reinterpret_cast<int4 *>(z + sub * PER + 4 * u) = make_int4(o[0], o[1], o[2], o[3]);
-            }
-            __syncwarp(team);
+    int *zb = zs + tm * S::STRIDE;
+    if (sub == 0) zb[8] = 0;
+    const int64_t wstep = (int64_t)gridDim.x * (kResolveThreads / 32) * 32;
+    for (int64_t base = ((int64_t)blockIdx.x * (kResolveThreads / 32) + (threadIdx.x >> 5)) * 32; base < nrows;
+         base += wstep) {
+        // one row per lane: its list, ids and centre, 32 rows' loads in flight
+        const int64_t r = base + lane;
+        int4 ix = make_int4(-1, -1, -1, -1);
+        int fr = 0, ngf = 0;
+        uint64_t cw0 = 0, cw1 = 0;
+        if (r < nrows) {
+            const float4 v = reinterpret_cast<const float4 *>(a.topk_val)[r];
+            ix = reinterpret_cast<const int4 *>(a.topk_idx)[r];
+            const int t = a.rows ? a.rows[r] : (int)r;
+            const int slot = a.row_frame ? a.row_frame[r] : t / a.L;
+            fr = a.row_frame ? a.row_frame[r] : a.slot_frame[slot];
+            cw0 = a.cw[(int64_t)t * W];
+            if (W > 1) cw1 = a.cw[(int64_t)t * W + 1];
+            // the re-rank's band (same arithmetic as the hop kernel)
+            const float thr = __fadd_ru(v.x, __fmul_ru(2.0f, kEpsScale * a.l1[slot]));
+            const bool full = ix.w >= 0 && v.w <= thr;
+            const int ng = full ? 4 : (ix.x >= 0 && v.x <= thr) + (ix.y >= 0 && v.y <= thr) + (ix.z >= 0 && v.z <= thr);
+            ngf = ng | (full ? 8 : 0);
         }
-        int best = INT_MAX, bp = INT_MAX, gp[4] = {-1, -1, -1, -1};
-        for (int q = 0; q < ng; ++q) {
-            const int g = q == 0 ? ix.x : q == 1 ? ix.y : q == 2 ? ix.z : ix.w;
-            const int p = g * kGroupCols + sub;
-            int sum = INT_MAX, pp = INT_MAX;
-            if (p < P) {
-                const uint32_t *supp = c.pat_supp + (int64_t)p * wq;
-                sum = 0;
-                for (int q0 = 0; q0 < wq; q0 += 4) {
-                    uint32_t wd[4];
-                    support_words(supp, wq, q0, wd);
+        // eight rounds: team tq resolves the warp's row 4 k + tq
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k) {
+            const int src = 4 * k + tq;
+            const int rngf = __shfl_sync(0xffffffffu, ngf, src);
+            const int rfr = __shfl_sync(0xffffffffu, fr, src);
+            uint64_t rcw = __shfl_sync(0xffffffffu, cw0, src);
+            if constexpr (W > 1) {
+                const uint64_t rc1 = __shfl_sync(0xffffffffu, cw1, src);
+                if (sub * PER >= 64) rcw = rc1;
+            }
+            int4 rix;
+            rix.x = __shfl_sync(0xffffffffu, ix.x, src);
+            rix.y = __shfl_sync(0xffffffffu, ix.y, src);
+            rix.z = __shfl_sync(0xffffffffu, ix.z, src);
+            rix.w = __shfl_sync(0xffffffffu, ix.w, src);
+            const int ng = rngf & 7;
+            if (ng == 0) continue;  // past the end, or nothing kept: the list stays as it is
+            // stage z: lane sub converts samples [PER sub, PER sub + PER)
+            {
+                const float4 *yr = reinterpret_cast<const float4 *>(a.y + (int64_t)rfr * N + sub * PER);
+                float f[PER];
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int j = (int)((wd[e >> 2] >> (8 * (e & 3))) & 255u);
-                        sum += z[min(j, N)];  // index N (padding) reads 0
+                for (int u = 0; u < PER / 4; ++u) {
+                    const float4 q = yr[u];
+                    f[4 * u] = q.x;
+                    f[4 * u + 1] = q.y;
+                    f[4 * u + 2] = q.z;
+                    f[4 * u + 3] = q.w;
+                }
+                __syncwarp(team);  // the previous row's sums are done
+#pragma unroll
+                for (int e = 0; e < PER; ++e) {
+                    const int j = sub * PER + e;
+                    const int g = grid_q(f[e]);
+                    zb[e * 9 + sub] = ((rcw >> (j & 63)) & 1ull) ? -g : g;
+                }
+                __syncwarp(team);
+            }
+            int best = INT_MAX, bp = INT_MAX, gp[4] = {-1, -1, -1, -1};
+            for (int q = 0; q < ng; ++q) {
+                const int g = q == 0 ? rix.x : q == 1 ? rix.y : q == 2 ? rix.z : rix.w;
+                const int p = g * kGroupCols + sub;
+                int sum = INT_MAX, pp = INT_MAX;
+                if (p < P) {
+                    const uint32_t *supp = c.pat_supp + (int64_t)p * wq;
+                    sum = 0;
+                    for (int q0 = 0; q0 < wq; q0 += 4) sum += team_sum16<N>(zb, supp_quad<N>(supp, wq, q0));
+                    pp = p;
+                }
+#pragma unroll
+                for (int o = 4; o >= 1; o >>= 1) {
+                    const int s2 = __shfl_xor_sync(team, sum, o), p2 = __shfl_xor_sync(team, pp, o);
+                    if (s2 < sum || (s2 == sum && p2 < pp)) {
+                        sum = s2;
+                        pp = p2;
                     }
                 }
-                pp = p;
-            }
-#pragma unroll
-            for (int o = 4; o >= 1; o >>= 1) {
-                const int s2 = __shfl_xor_sync(team, sum, o), p2 = __shfl_xor_sync(team, pp, o);
-                if (s2 < sum || (s2 == sum && p2 < pp)) {
-                    sum = s2;
-                    pp = p2;
+                gp[q] = pp;
+                if (sum < best || (sum == best && pp < bp)) {
+                    best = sum;
+                    bp = pp;
                 }
             }
-            gp[q] = pp;
-            if (sum < best || (sum == best && pp < bp)) {
-                best = sum;
-                bp = pp;
+            if (sub != 0) continue;
+            const int64_t rr = base + src;
+            if (rngf & 8) {
+                reinterpret_cast<int4 *>(a.topk_idx)[rr] = make_int4(gp[0], gp[1], gp[2], gp[3]);
+            } else {
+                reinterpret_cast<float4 *>(a.topk_val)[rr] =
+                    make_float4((float)best * (1.0f / 524288.0f), a.exact_tag ? __int_as_float(best) : CUDART_INF_F,
+                                CUDART_INF_F, CUDART_INF_F);
+                reinterpret_cast<int4 *>(a.topk_idx)[rr] = make_int4(bp, a.exact_tag ? kExactTag : -1, -1, -1);
             }
         }
-        if (sub != 0) continue;
-        if (full) {
-            reinterpret_cast<int4 *>(a.topk_idx)[r] = make_int4(gp[0], gp[1], gp[2], gp[3]);
-        } else {
-            reinterpret_cast<float4 *>(a.topk_val)[r] =
-                make_float4((float)best * (1.0f / 524288.0f), a.exact_tag ? __int_as_float(best) : CUDART_INF_F,
-                            CUDART_INF_F, CUDART_INF_F);
-            reinterpret_cast<int4 *>(a.topk_idx)[r] = make_int4(bp, a.exact_tag ? kExactTag : -1, -1, -1);
-        }
     }
+}
+
+template <int N>
+cudaError_t launch_resolve_n(const CodeDev &c, const ScoreArgs &a, cudaStream_t s) {
+    static int per_sm = 0;  // resident blocks per SM (registers, shared memory)
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resolve_groups_kernel<N>,
+                                                                      kResolveThreads, 0);
+        if (e != cudaSuccess) return e;
+        per_sm = std::max(per_sm, 1);
+    }
+    int64_t grid = (int64_t)c.num_sms * per_sm;
+    if (!a.n_rows_dev) grid = std::min<int64_t>(grid, (a.n_rows + kResolveThreads - 1) / kResolveThreads);
+    if (grid <= 0) return cudaSuccess;
+    resolve_groups_kernel<N><<<(unsigned)grid, kResolveThreads, 0, s>>>(a, c);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_resolve_groups(const CodeDev &c, const ScoreArgs &a, cudaStream_t s) {
-    int64_t grid = (int64_t)c.num_sms * 8;
-    if (!a.n_rows_dev) grid = std::min<int64_t>(grid, (a.n_rows + kResolveTeams - 1) / kResolveTeams);
-    if (grid <= 0) return cudaSuccess;
-    if (c.n == 64)
-        resolve_groups_kernel<64><<<(unsigned)grid, kResolveThreads, 0, s>>>(a, c);
-    else if (c.n == 128)
-        resolve_groups_kernel<128><<<(unsigned)grid, kResolveThreads, 0, s>>>(a, c);
-    else
-        return cudaErrorNotSupported;
-    return cudaGetLastError();
+    if (c.n == 64) return launch_resolve_n<64>(c, a, s);
+    if (c.n == 128) return launch_resolve_n<128>(c, a, s);
+    return cudaErrorNotSupported;
 }
 
 cudaError_t launch_split_prep(const CodeDev &c, const float *y, int64_t B, uint32_t *yhl, float *l1, cudaStream_t s) {
