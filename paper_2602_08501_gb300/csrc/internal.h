@@ -104,6 +104,7 @@ struct CodeDev {
     bool trailing_frozen = false; // a frozen leaf follows the last information leaf
     int w_max = 0;                // largest pattern weight
     int wq_max = 0;               // support words per pattern (4 indices per word)
+    bool supp_dense = false;      // every pattern has weight 4 wq_max: no padding entries
     // device arrays
     uint64_t *pat_bits = nullptr;   // P x W
     uint32_t *pat_supp = nullptr;   // P x wq_max, 4 uint8 indices per word, padded with index n

@@ -364,11 +364,13 @@ extern "C" int mpwsd_load_code(int n, const uint8_t *G, const uint8_t *frozen, i
 
     // host images
     std::vector<uint32_t> supp((size_t)n_patterns * d.wq_max, 0);
+    d.supp_dense = true;
     for (int64_t p = 0; p < n_patterns; ++p) {
         uint8_t idx[128];
         int w = 0;
         for (int j = 0; j < n; ++j)
             if ((patterns[p * W + j / 64] >> (j % 64)) & 1ull) idx[w++] = (uint8_t)j;
+        if (w != d.wq_max * 4) d.supp_dense = false;
         for (; w < d.wq_max * 4; ++w) idx[w] = (uint8_t)n;  // pad: reads the zero slot
         for (int q = 0; q < d.wq_max; ++q)
             supp[(size_t)p * d.wq_max + q] = (uint32_t)idx[4 * q] | ((uint32_t)idx[4 * q + 1] << 8) |

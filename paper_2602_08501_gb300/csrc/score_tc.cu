@@ -51,36 +51,33 @@ __global__ void __launch_bounds__(256) split_prep_kernel(const float *y, int64_t
 // values, each group replaced by its pattern of smallest exact score, so every
 // value stays within eps of its pattern's exact score.
 //
-// Shared layout of a team's row: sample j at (j % PER) * 9 + j / PER (PER =
-// N / 8 samples per lane); slot 8 holds 0 and serves the support padding
-// (index N, and 255 past a pattern's words). Staging stores are then free of
-// bank conflicts: the team regions start 8 banks apart.
+// A team's row sits in shared memory in sample order, with a zero at index N
+// that the support padding (index N, and 255 past a pattern's words, clamped)
+// reads; pattern sets without padding skip the clamp.
 constexpr int kResolveThreads = 256;
 constexpr int kResolveTeams = kResolveThreads / kGroupCols;
 
 template <int N>
 struct ResolveShape {
-    static constexpr int PER = N / kGroupCols;                  // samples per lane (8 or 16)
-    static constexpr int SH = PER == 8 ? 3 : 4;                  // log2 PER
-    static constexpr int STRIDE = PER == 8 ? 72 : 168;           // team region, = 8 (mod 32) ints
-    static_assert(STRIDE >= PER * 9 && STRIDE % 32 == 8, "team regions 8 banks apart");
+    static constexpr int PER = N / kGroupCols;          // samples per lane (8 or 16)
+    static constexpr int STRIDE = N + 8;                 // team region, = 8 (mod 32) ints
+    static_assert(STRIDE > N && STRIDE % 32 == 8, "team regions 8 banks apart");
 };
 
 // sum of z over 16 support indices (4 words of 4 uint8 indices)
-template <int N>
+template <int N, bool DENSE>
 __device__ __forceinline__ int team_sum16(const int *zb, const uint4 w) {
-    using S = ResolveShape<N>;
     const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
     int sum = 0;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-        const int j = min((int)((wd[e >> 2] >> (8 * (e & 3))) & 255u), N);
-        sum += zb[(j & (S::PER - 1)) * 9 + (j >> S::SH)];
+        int j = (int)__byte_perm(wd[e >> 2], 0u, 0x4440u + (uint32_t)(e & 3));
+        if constexpr (!DENSE) j = min(j, N);
+        sum += zb[j];
     }
     return sum;
 }
 
-template <int N>
 __device__ __forceinline__ uint4 supp_quad(const uint32_t *supp, int wq, int q0) {
     if ((wq & 3) == 0) return __ldg(reinterpret_cast<const uint4 *>(supp + q0));
     uint32_t wd[4];
@@ -88,7 +85,7 @@ __device__ __forceinline__ uint4 supp_quad(const uint32_t *supp, int wq, int q0)
     return make_uint4(wd[0], wd[1], wd[2], wd[3]);
 }
 
-template <int N>
+template <int N, bool DENSE>
 __global__ void __launch_bounds__(kResolveThreads) resolve_groups_kernel(const ScoreArgs a, const CodeDev c) {
     static_assert(kGroupCols == 8, "one 8-lane team per row");
     using S = ResolveShape<N>;
@@ -100,7 +97,7 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_groups_kernel(const S
     const unsigned team = 0xffu << (lane & 24);
     const int wq = c.wq_max, P = (int)c.P;
     int *zb = zs + tm * S::STRIDE;
-    if (sub == 0) zb[8] = 0;
+    if (sub == 0) zb[N] = 0;
     const int64_t wstep = (int64_t)gridDim.x * (kResolveThreads / 32) * 32;
     for (int64_t base = ((int64_t)blockIdx.x * (kResolveThreads / 32) + (threadIdx.x >> 5)) * 32; base < nrows;
          base += wstep) {
@@ -155,10 +152,15 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_groups_kernel(const S
                 }
                 __syncwarp(team);  // the previous row's sums are done
 #pragma unroll
-                for (int e = 0; e < PER; ++e) {
-                    const int j = sub * PER + e;
-                    const int g = grid_q(f[e]);
-                    zb[e * 9 + sub] = ((rcw >> (j & 63)) & 1ull) ? -g : g;
+                for (int u = 0; u < PER / 4; ++u) {
+                    int o[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int j = sub * PER + 4 * u + e;
+                        const int g = grid_q(f[4 * u + e]);
+                        o[e] = ((rcw >> (j & 63)) & 1ull) ? -g : g;
+                    }
+                    *reinterpret_cast<int4 *>(zb + sub * PER + 4 * u) = make_int4(o[0], o[1], o[2], o[3]);
                 }
                 __syncwarp(team);
             }
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_groups_kernel(const S
                 if (p < P) {
                     const uint32_t *supp = c.pat_supp + (int64_t)p * wq;
                     sum = 0;
-                    for (int q0 = 0; q0 < wq; q0 += 4) sum += team_sum16<N>(zb, supp_quad<N>(supp, wq, q0));
+                    for (int q0 = 0; q0 < wq; q0 += 4) sum += team_sum16<N, DENSE>(zb, supp_quad(supp, wq, q0));
                     pp = p;
                 }
 #pragma unroll
@@ -201,11 +203,11 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_groups_kernel(const S
     }
 }
 
-template <int N>
+template <int N, bool DENSE>
 cudaError_t launch_resolve_n(const CodeDev &c, const ScoreArgs &a, cudaStream_t s) {
     static int per_sm = 0;  // resident blocks per SM (registers, shared memory)
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resolve_groups_kernel<N>,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resolve_groups_kernel<N, DENSE>,
                                                                       kResolveThreads, 0);
         if (e != cudaSuccess) return e;
         per_sm = std::max(per_sm, 1);
@@ -213,15 +215,16 @@ cudaError_t launch_resolve_n(const CodeDev &c, const ScoreArgs &a, cudaStream_t 
     int64_t grid = (int64_t)c.num_sms * per_sm;
     if (!a.n_rows_dev) grid = std::min<int64_t>(grid, (a.n_rows + kResolveThreads - 1) / kResolveThreads);
     if (grid <= 0) return cudaSuccess;
-    resolve_groups_kernel<N><<<(unsigned)grid, kResolveThreads, 0, s>>>(a, c);
+    resolve_groups_kernel<N, DENSE><<<(unsigned)grid, kResolveThreads, 0, s>>>(a, c);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_resolve_groups(const CodeDev &c, const ScoreArgs &a, cudaStream_t s) {
-    if (c.n == 64) return launch_resolve_n<64>(c, a, s);
-    if (c.n == 128) return launch_resolve_n<128>(c, a, s);
+    if (c.n == 64) return c.supp_dense ? launch_resolve_n<64, true>(c, a, s) : launch_resolve_n<64, false>(c, a, s);
+    if (c.n == 128)
+        return c.supp_dense ? launch_resolve_n<128, true>(c, a, s) : launch_resolve_n<128, false>(c, a, s);
     return cudaErrorNotSupported;
 }
 
