@@ -119,6 +119,13 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_groups_kernel(const S
             const bool full = ix.w >= 0 && v.w <= thr;
             const int ng = full ? 4 : (ix.x >= 0 && v.x <= thr) + (ix.y >= 0 && v.y <= thr) + (ix.z >= 0 && v.z <= thr);
             ngf = ng | (full ? 8 : 0);
+            // decode: when even the smallest approximate score exceeds eps, no pattern
+            // has a negative exact score (no strict improvement) and the row stops;
+            // there is nothing to resolve (the tag with no pattern tells the hop)
+            if (a.exact_tag && v.x > kEpsScale * a.l1[slot]) {
+                ngf = 0;
+                reinterpret_cast<int4 *>(a.topk_idx)[r] = make_int4(-1, kExactTag, -1, -1);
+            }
         }
         // eight rounds: team tq resolves the warp's row 4 k + tq
 #pragma unroll 1

@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(kHopThreads) hop_kernel(const Workspace ws, co
             const double D = ws.traj_D[t];
             const uint32_t st = ws.traj_state[t];
             // a row resolved from tensor-core candidate groups carries the exact sum
-            // of its single candidate in slot 1 (tag kExactTag)
+            // of its single candidate in slot 1 (tag kExactTag); no candidate (slot 0
+            // index -1) means no pattern improves on the centre
             const bool tagged = ix.y == kExactTag;
             uint32_t wd0[4];
             if (!tagged) support_words(c.pat_supp + (int64_t)max(ix.x, 0) * wq, wq, 0, wd0);
