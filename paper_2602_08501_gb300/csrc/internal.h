@@ -17,9 +17,6 @@ __host__ __device__ constexpr int tc_patterns_per_tile(int n) { return n == 64 ?
 // patterns (group g: patterns 8g .. 8g + 7); resolve_groups_kernel scores their
 // patterns exactly and leaves the argmin pattern.
 constexpr int kGroupCols = 8;
-// List slot 1 of a resolved row: index kExactTag, value = the exact integer
-// sum (2^-19 grid units) of slot 0's pattern, bit-cast to float.
-constexpr int kExactTag = -2;
 constexpr int kGridShift = 19;            // y is read on the 2^-19 grid
 constexpr int kGridMax = (1 << 23) - 1;   // |round(y 2^19)| <= 2^23 - 1
 // Margin of the near-tie re-rank: every approximate score is within
@@ -199,9 +196,6 @@ struct ScoreArgs {
     int *split_idx;
     int *unit_done;
     int split_items;  // target work items of the split (<= kSplitItemsPerSm / 2 x SMs)
-    // decode: the group resolution also leaves the exact integer sum of the row's
-    // argmin in list slot 1 (tagged kExactTag) so the re-rank need not recompute it
-    bool exact_tag;
 };
 
 // Launchers (return cudaError_t of the launch).
@@ -221,8 +215,11 @@ cudaError_t launch_score_fp32(const CodeDev &c, const ScoreArgs &a, cudaStream_t
 // Exact scoring of a flat pattern set by Walsh-Hadamard coefficients (score_flats.cu)
 cudaError_t launch_score_flats(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
 cudaError_t launch_score_tc(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
-// exact argmin pattern of each row from the candidate groups launch_score_tc keeps
-cudaError_t launch_resolve_groups(const CodeDev &c, const ScoreArgs &a, cudaStream_t s);
+// exact argmin pattern of each row from the candidate groups launch_score_tc keeps;
+// with a workspace (a decode's iteration `iter`), the hop decision of each row
+// as well (in place of launch_hop), the lists left unwritten
+cudaError_t launch_resolve_groups(const CodeDev &c, const ScoreArgs &a, const Workspace *ws, int iter,
+                                  cudaStream_t s);
 // y (B x n) -> bf16 hi / lo words and ||y||_1 per frame, for direct-mode tensor-core scoring
 cudaError_t launch_split_prep(const CodeDev &c, const float *y, int64_t B, uint32_t *yhl, float *l1, cudaStream_t s);
 bool score_tc_supported(const CodeDev &c);

@@ -648,7 +648,25 @@ static cudaError_t launch_score(mpwsd_code *code, int mode, const ScoreArgs &a, 
     // tensor cores keep candidate groups; their exact argmin follows in its own kernel
     cudaError_t e = timed_launch(code, MPWSD_KERNEL_SCORE_TC, s, [&] { return launch_score_tc(code->d, a, s); });
     if (e != cudaSuccess) return e;
-    return timed_launch(code, MPWSD_KERNEL_RESOLVE, s, [&] { return launch_resolve_groups(code->d, a, s); });
+    return timed_launch(code, MPWSD_KERNEL_RESOLVE, s,
+                        [&] { return launch_resolve_groups(code->d, a, nullptr, 0, s); });
+}
+
+// One scoring step of stage 2 and the re-rank / hop decision of its rows
+// (iteration `iter` of a decode, or a pool step): with tensor-core scoring the
+// group resolution takes the decisions itself; the other forms leave their
+// lists to the hop kernel.
+static cudaError_t score_and_hop(mpwsd_code *code, int mode, const ScoreArgs &a, const Workspace &ws, int iter, int L,
+                                 const float *y, cudaStream_t s) {
+    if (mode == MPWSD_SCORE_BF16X2) {
+        cudaError_t e = timed_launch(code, MPWSD_KERNEL_SCORE_TC, s, [&] { return launch_score_tc(code->d, a, s); });
+        if (e != cudaSuccess) return e;
+        return timed_launch(code, MPWSD_KERNEL_RESOLVE, s,
+                            [&] { return launch_resolve_groups(code->d, a, &ws, iter, s); });
+    }
+    cudaError_t e = launch_score(code, mode, a, s);
+    if (e != cudaSuccess) return e;
+    return timed_launch(code, MPWSD_KERNEL_HOP, s, [&] { return launch_hop(code->d, ws, iter, L, y, s); });
 }
 
 // Host buffers of mpwsd_decode_host: y is copied in chunk by chunk on the copy
@@ -741,11 +759,8 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
         a.split_idx = ws.split_idx;
         a.unit_done = ws.unit_done;
         a.split_items = d.split_items;
-        a.exact_tag = true;
-        e = launch_score(code, o.score_mode, a, s);
-        if (e != cudaSuccess) return cuda_fail(e, "scoring launch");
-        e = timed_launch(code, MPWSD_KERNEL_HOP, s, [&] { return launch_hop(d, ws, it, L, y_dev, s); });
-        if (e != cudaSuccess) return cuda_fail(e, "hop launch");
+        e = score_and_hop(code, o.score_mode, a, ws, it, L, y_dev, s);
+        if (e != cudaSuccess) return cuda_fail(e, "scoring / hop launch");
         e = timed_launch(code, MPWSD_KERNEL_RESCAN, s, [&] { return launch_rescan(d, ws, it, L, y_dev, s); });
         if (e != cudaSuccess) return cuda_fail(e, "rescan launch");
         if (it + 1 < T) {
@@ -1312,13 +1327,11 @@ static int pool_step_launches(mpwsd_pool *p, cudaStream_t s) {
     a.split_idx = ws.split_idx;
     a.unit_done = ws.unit_done;
     a.split_items = d.split_items;
-    a.exact_tag = true;
-    cudaError_t e = launch_score(code, p->o.score_mode, a, s);
-    if (e != cudaSuccess) return cuda_fail(e, "scoring launch");
     const float *y = ws.pool.slot_y;
     const int L = p->L;
-    e = timed_launch(code, MPWSD_KERNEL_HOP, s, [&] { return launch_hop(d, ws, 0, L, y, s); });
-    if (e == cudaSuccess) e = timed_launch(code, MPWSD_KERNEL_RESCAN, s, [&] { return launch_rescan(d, ws, 0, L, y, s); });
+    cudaError_t e = score_and_hop(code, p->o.score_mode, a, ws, 0, L, y, s);
+    if (e != cudaSuccess) return cuda_fail(e, "scoring / hop launch");
+    e = timed_launch(code, MPWSD_KERNEL_RESCAN, s, [&] { return launch_rescan(d, ws, 0, L, y, s); });
     if (e == cudaSuccess) e = timed_launch(code, MPWSD_KERNEL_HOP, s, [&] { return launch_dedup(d, ws, 0, L, s); });
     if (e == cudaSuccess) e = timed_launch(code, MPWSD_KERNEL_FINAL, s, [&] { return launch_pool_final(d, ws, L, s); });
     if (e == cudaSuccess) e = timed_launch(code, MPWSD_KERNEL_FINAL, s, [&] { return launch_pool_end(d, ws, s); });

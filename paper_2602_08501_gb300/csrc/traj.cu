@@ -51,12 +51,8 @@ __global__ void __launch_bounds__(kHopThreads) hop_kernel(const Workspace ws, co
             const uint64_t c0 = cwp[0], c1 = W > 1 ? cwp[1] : 0ull;
             const double D = ws.traj_D[t];
             const uint32_t st = ws.traj_state[t];
-            // a row resolved from tensor-core candidate groups carries the exact sum
-            // of its single candidate in slot 1 (tag kExactTag); no candidate (slot 0
-            // index -1) means no pattern improves on the centre
-            const bool tagged = ix.y == kExactTag;
             uint32_t wd0[4];
-            if (!tagged) support_words(c.pat_supp + (int64_t)max(ix.x, 0) * wq, wq, 0, wd0);
+            support_words(c.pat_supp + (int64_t)max(ix.x, 0) * wq, wq, 0, wd0);
             const float *yr = y + (int64_t)frame * n;
             const float thr = __fadd_ru(v.x, __fmul_ru(2.0f, kEpsScale * l1));
             if (ix.w >= 0 && v.w <= thr) {
@@ -66,12 +62,8 @@ __global__ void __launch_bounds__(kHopThreads) hop_kernel(const Workspace ws, co
                 const int ncand = (ix.x >= 0 && v.x <= thr) + (ix.y >= 0 && v.y <= thr) + (ix.z >= 0 && v.z <= thr);
                 double best = CUDART_INF;
                 int bp = -1;
-                if (tagged) {
-                    best = (double)__float_as_int(v.y) * (1.0 / 524288.0);
-                    bp = ix.x;
-                }
 #pragma unroll 1
-                for (int q = 0; q < (tagged ? 0 : ncand); ++q) {
+                for (int q = 0; q < ncand; ++q) {
                     const int p = q == 0 ? ix.x : q == 1 ? ix.y : ix.z;
                     const uint32_t *supp = c.pat_supp + (int64_t)p * wq;
                     // wave 3 for the first candidate: its first support words are in hand
