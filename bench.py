@@ -580,35 +580,49 @@ def run_ours(args, wl_cfg):
                     "frac": ach / (alu_peak / 1e12), "traffic": tr, "traffic_source": traffic_note, "kernel": "osd",
                     "peak_kind": "152 SMs x 128 INT32 lanes x max SM clock", "ops_per_launch": ops}
         if kname == "hop":
-            # bytes a row needs: its list entry (4 + 32), centre, D, state, 1/L of its frame's y row and
-            # slot data, the supports of its candidates, and on a hop the written centre, D, state, entry
             rows = evals / P if P else 0.0
             wq = math.ceil(wmax / 4)
             cand = stats["rerank_candidates"] / rows if rows else 0.0
             hopf = stats["hops"] / rows if rows else 0.0
-            if args.mode == "bf16x2":
-                # rows resolved from tensor-core groups carry their exact sum: no supports, no y
-                bpr = 36 + 8 * W + 12 + hopf * (8 * W + 16)
-            else:
-                bpr = 36 + 8 * W + 12 + (4 * n + 8) / L + cand * 4 * wq + hopf * (8 * W + 16)
-            ach = bpr * rows / launches / per_launch_s / 1e9
             src = src_hash("paper_2602_08501_gb300/csrc/traj.cu", "paper_2602_08501_gb300/csrc/common.cuh",
                            "paper_2602_08501_gb300/csrc/internal.h")
+            if args.mode == "bf16x2":
+                # the class holds the twin retirement alone (the resolution kernel takes the
+                # hop decisions): per hopped row its entry, its centre, the centres and states
+                # of the (L - 1) / 2 lower-numbered trajectories of its frame on average, and
+                # its next-iteration entry
+                units = stats["hops"]
+                bpr = 4 + 8 * W + (L - 1) / 2 * (8 * W + 4) + 4
+                ach = bpr * units / launches / per_launch_s / 1e9
+                return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "hop",
+                        "peak_kind": f"HBM copy, {peaks['source']}", "bytes_per_hopped_row": bpr,
+                        "note": "twin retirement only (the resolution kernel takes the hop decisions)"}
+            # bytes a row needs: its list entry (4 + 32), centre, D, state, 1/L of its frame's y row and
+            # slot data, the supports of its candidates, and on a hop the written centre, D, state, entry
+            bpr = 36 + 8 * W + 12 + (4 * n + 8) / L + cand * 4 * wq + hopf * (8 * W + 16)
+            ach = bpr * rows / launches / per_launch_s / 1e9
             rec = recorded_traffic("hop", src, "row")
             tr = None if rec is None else rec * rows / launches
             return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": ach / peaks["hbm_gbs"], "traffic": tr, "traffic_source": traffic_note, "kernel": "hop",
                     "peak_kind": f"HBM copy, {peaks['source']}", "bytes_per_row": bpr}
         if kname == "resolve":
-            # bytes a row needs: its list in and out (36 + 32), row / slot / frame ids, centre, 1/L of
-            # its frame's y row, and the supports of one group of kGroupCols = 8 patterns
+            # bytes a row needs: its list (32), row / slot / frame ids and ||y||_1 (12), centre, D and
+            # state (12), 1/L of its frame's y row, the supports of one group of kGroupCols = 8
+            # patterns, and on a hop the written centre, D and state plus its entry (8W + 16)
             rows = evals / P if P else 0.0
             wq = math.ceil(wmax / 4)
-            bpr = 36 + 32 + 12 + 8 * W + (4 * n + 8) / L + 8 * 4 * wq
+            hopf = stats["hops"] / rows if rows else 0.0
+            bpr = 32 + 12 + 8 * W + 12 + (4 * n + 8) / L + 8 * 4 * wq + hopf * (8 * W + 16)
             ach = bpr * rows / launches / per_launch_s / 1e9
+            src = src_hash("paper_2602_08501_gb300/csrc/score_tc.cu", "paper_2602_08501_gb300/csrc/common.cuh",
+                           "paper_2602_08501_gb300/csrc/internal.h")
+            rec = recorded_traffic("resolve", src, "row")
+            tr = None if rec is None else rec * rows / launches
             return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "resolve",
-                    "peak_kind": f"HBM copy, {peaks['source']}", "bytes_per_row": bpr}
+                    "frac": ach / peaks["hbm_gbs"], "traffic": tr, "traffic_source": traffic_note,
+                    "kernel": "resolve", "peak_kind": f"HBM copy, {peaks['source']}", "bytes_per_row": bpr}
         return {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
                 "kernel": kname}
 

@@ -404,12 +404,14 @@ MPWSD_API int mpwsd_sync(mpwsd_code *code, void *stream);
 #define MPWSD_KERNEL_SCL 0        /* stage 1: SC-list + CRC + compaction */
 #define MPWSD_KERNEL_SCORE_TC 1   /* scoring, tcgen05 BF16 hi+lo */
 #define MPWSD_KERNEL_SCORE_FP32 2 /* scoring, FP32 CUDA cores */
-#define MPWSD_KERNEL_HOP 3        /* FP64 near-tie re-rank + hop + compaction, and twin retirement */
+#define MPWSD_KERNEL_HOP 3        /* FP64 near-tie re-rank + hop + compaction (FP32 and FLATS scoring), and twin
+                                     retirement */
 #define MPWSD_KERNEL_RESCAN 4     /* full FP64 rescan of overflowing rows */
 #define MPWSD_KERNEL_FINAL 5      /* per-frame argmin ED + flags */
 #define MPWSD_KERNEL_OSD 6        /* stage 1 by OSD(order) + CRC + compaction */
 #define MPWSD_KERNEL_SCORE_FLATS 7 /* scoring, exact Walsh-Hadamard coset sums (MPWSD_SCORE_FLATS) */
-#define MPWSD_KERNEL_RESOLVE 8    /* exact argmin inside the candidate groups of the tcgen05 scoring */
+#define MPWSD_KERNEL_RESOLVE 8    /* exact argmin inside the candidate groups of the tcgen05 scoring; in a
+                                     decode also the re-rank decision, hop and compaction of each row */
 #define MPWSD_KERNEL_KINDS 9
 
 typedef struct mpwsd_kernel_time {

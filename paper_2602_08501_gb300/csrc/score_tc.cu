@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(256) split_prep_kernel(const float *y, int64_t
 //
 // Mapping: a warp takes 32 rows, one per lane, and loads their lists, ids and
 // centres with 32 rows' loads in flight; then eight rounds, in each of which
-// its four 8-lane teams resolve one row each.
+// its four 8-lane teams resolve one row each (small batches: fewer rows and
+// rounds per warp, so that every warp has work).
 //
 // Two uses. Alone (mpwsd_score_topk), the row's list becomes that one pattern
 // with its exact score; a full list keeps its four values, each group replaced
@@ -110,12 +111,18 @@ __global__ void __launch_bounds__(kResolveThreads)
     int *zb = zs + tm * S::STRIDE;
     if (sub == 0) zb[N] = 0;
     unsigned long long my_cand = 0, my_hops = 0;
-    const int64_t wstep = (int64_t)gridDim.x * (kResolveThreads / 32) * 32;
-    for (int64_t base = ((int64_t)blockIdx.x * (kResolveThreads / 32) + (threadIdx.x >> 5)) * 32; base < nrows;
+    // rows per warp pass: 32 when there are enough rows, fewer (a multiple of 4)
+    // when a small batch would otherwise leave warps idle while others run eight
+    // rounds one after another
+    const int64_t nwarps = (int64_t)gridDim.x * (kResolveThreads / 32);
+    const int64_t per = (((int64_t)nrows + nwarps - 1) / nwarps + 3) & ~(int64_t)3;
+    const int rpw = per < 32 ? (int)per : 32;
+    const int64_t wstep = nwarps * rpw;
+    for (int64_t base = ((int64_t)blockIdx.x * (kResolveThreads / 32) + (threadIdx.x >> 5)) * rpw; base < nrows;
          base += wstep) {
         // one row per lane: its list, ids and centre (and, with the hop, its D and
         // state), 32 rows' loads in flight
-        const int64_t r = base + lane;
+        const int64_t r = lane < rpw ? base + lane : (int64_t)nrows;  // lanes past rpw hold no row
         int4 ix = make_int4(-1, -1, -1, -1);
         int fr = 0, ngf = 0, t = 0;
         uint64_t cw0 = 0, cw1 = 0;
@@ -145,9 +152,9 @@ __global__ void __launch_bounds__(kResolveThreads)
             if (HOP && !full && v.x > kEpsScale * l1) ngf = 0;
         }
         int my_best = INT_MAX, my_bp = -1;
-        // eight rounds: team tq resolves the warp's row 4 k + tq
+        // rpw / 4 rounds: team tq resolves the warp's row 4 k + tq
 #pragma unroll 1
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < rpw / 4; ++k) {
             const int src = 4 * k + tq;
             const int rngf = __shfl_sync(0xffffffffu, ngf, src);
             const int rfr = __shfl_sync(0xffffffffu, fr, src);
