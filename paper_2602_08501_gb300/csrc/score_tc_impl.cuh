@@ -728,8 +728,11 @@ __global__ void __launch_bounds__(TcCfg<N, BN_, BLD, BST>::THREADS, 1) score_tc_
                     ti[rbx][k] = -1;
                 }
                 thr[rbx] = CUDART_INF_F;
-                // 2 eps of this row (the re-rank margin), from ||y||_1 of its frame
-                eps2[rbx] = __fmul_ru(2.0f * kEpsScale, __fmul_ru(sh.l1[ab * UM + rbx * BM + r], 1.0f + 1.0f / 1024.0f));
+                // 2 eps of this row (the re-rank margin), from ||y||_1 of its frame, and at
+                // least the smallest normal float: with y = 0 every score ties at 0, and a
+                // zero margin would admit only the first of them where the band holds all
+                eps2[rbx] = fmaxf(__fmul_ru(2.0f * kEpsScale, __fmul_ru(sh.l1[ab * UM + rbx * BM + r], 1.0f + 1.0f / 1024.0f)),
+                                  1.17549435e-38f);
             }
             mbar_arrive(smem_u32(&sh.l1_free[ab]));
             for (int j = ch * nt / nch; j < (ch + 1) * nt / nch && ok; ++j, ++gacc) {

@@ -108,3 +108,43 @@ def test_decode_cfg4_patterns_bf16x2(mp, oracle_mod):
     _, fl, _ = _decode_parity(mp, code, ocode, wl, 32, 8, "bf16x2")
     assert np.sum(fl & 1) >= 100
     _decode_parity(mp, code, ocode, wl, 32, 8, "fp32")
+
+
+def test_tc_resolution_on_built_ties(mp, oracle_mod):
+    """Rows built to tie (+-1/2 on the union of two patterns, so their scores are
+    equal; y = 0, so every pattern ties): the resolved entry is the lowest index
+    among the exact minima with its exact score, or, when four candidate groups
+    share the band, a full list whose values lie within eps of their patterns'
+    exact scores."""
+    code = mp.Code.rm(6, 2, weights=[16])
+    ocode = oracle_code(oracle_mod, 6, 2, 0, [16])
+    n, B, M = 64, 40, 600
+    rng = np.random.default_rng(97)
+    y = synth.grid_quantize(rng.standard_normal((B, n)) * 1.3 + 0.2)
+    P = oracle_mod.unpack_bits(ocode.patterns, n)
+    for f, (p, q) in enumerate([(0, 1), (3, 40), (P.shape[0] - 1, 5), (7, 8), (100, 2000)]):
+        y[f] = np.where((P[p] | P[q]) == 1, -0.5, 0.5)
+    y[5] = 0.0
+    frame = rng.integers(0, B, M).astype(np.int32)
+    frame[:6] = np.arange(6)
+    centres = np.zeros((M, code.W), np.uint64)
+    for i in range(6, M):
+        for p in rng.integers(0, P.shape[0], 2):
+            centres[i] ^= ocode.patterns[p]
+    vals, idx = code.score_topk(_dev(y), _dev(frame, torch.int32), _dev(centres.view(np.int64), torch.int64), "bf16x2")
+    torch.cuda.synchronize()
+    vals, idx = vals.cpu().numpy(), idx.cpu().numpy()
+    fulls = 0
+    for i in range(M):
+        yy = y[frame[i]].astype(np.float64)
+        S = -ocode.gains(yy, oracle_mod.unpack_bits(centres[i], n)) / 2.0
+        eps = 2.0 ** -14 * np.abs(yy).sum()
+        cnt = int(np.sum(idx[i] >= 0))
+        if cnt == 4 and vals[i, 3] <= vals[i, 0] + 2 * eps:
+            fulls += 1
+            assert np.all(np.abs(vals[i] - S[idx[i]]) <= eps + 1e-12)
+            continue
+        want = int(np.flatnonzero(S == S.min())[0])
+        assert cnt == 1 and idx[i, 0] == want, (i, idx[i], want)
+        assert abs(vals[i, 0] - S.min()) <= 1e-6 * max(1.0, abs(S.min()))
+    assert fulls >= 1  # the y = 0 row fills the list
