@@ -96,6 +96,7 @@ struct SclCtx {
     const int *ych;                // channel LLRs of this frame (shared memory)
     int lane;                      // lane within the frame's segment
     int count;                     // current list size (uniform over the warp)
+    long long pref;                // lower bound on every path metric of the frame
     int L;
     uint64_t root_cw[2];           // root codeword when n = 128
     FZ fz;
@@ -149,6 +150,7 @@ __device__ __forceinline__ constexpr bool has_info() {
 // Outcome of the list step at an information leaf, for one lane.
 struct LeafStep {
     long long pm;   // new path metric (kept lanes)
+    long long pref; // smallest metric of the new list (a lower bound on every later one)
     int par;        // lane whose history this lane continues
     int count;      // new list size
     unsigned bit;   // decided u of this lane's path
@@ -193,18 +195,18 @@ __device__ __forceinline__ K seg_merge_low(K a, K b, int lane) {
 // distinct (parent position and bit are in them), so sorting them gives that
 // order exactly: the two children sets are sorted apart (bitonic networks
 // across the frame's lanes) and merged keeping the smallest LW, so lane r ends
-// with the r-th child. Metrics are taken relative to the frame's best path;
-// when every relative metric of the segment fits 25 bits the keys fit 32 bits
-// (the usual case), otherwise the same network runs on 64-bit keys.
+// with the r-th child. Metrics are taken relative to the smallest metric the
+// list had after the previous list step (metrics only grow, so none is
+// below it); when every relative metric of the segment fits 25 bits the keys
+// fit 32 bits (the usual case), otherwise the same network runs on 64-bit keys.
 template <int LW>
-__device__ __noinline__ LeafStep list_step(int lam, long long pm, int lane, int count, int L) {
+__device__ __noinline__ LeafStep list_step(int lam, long long pm, int lane, int count, int L, long long pref) {
     const unsigned hd = lam < 0 ? 1u : 0u;
     const long long a = lam < 0 ? -(long long)lam : (long long)lam;
     const bool valid = lane < count;
-    long long pmin = valid ? pm : 0x7fffffffffffffffLL;
-#pragma unroll
-    for (int o = LW / 2; o >= 1; o >>= 1) pmin = min(pmin, __shfl_xor_sync(kFull, pmin, o, LW));
-    const long long d0 = pm - pmin;
+    // metrics only grow, so the smallest metric after the last list step bounds every
+    // metric now from below: keys relative to it are non-negative
+    const long long d0 = pm - pref;
     const bool small = !valid || d0 + a < (1LL << 25);
     const int nc = min(2 * count, L);
     const bool keep = lane < nc;
@@ -216,8 +218,9 @@ __device__ __noinline__ LeafStep list_step(int lam, long long pm, int lane, int 
         const uint32_t q1 = valid ? (((uint32_t)(d0 + a) << 6) | base32 | (hd ^ 1u)) : 0xffffffffu;
         const uint32_t kk = seg_merge_low<LW>(seg_sort<LW>(q0, lane), seg_sort<LW>(q1, lane), lane);
         out.par = keep ? (int)((kk >> 1) & 31u) : lane;
-        out.pm = keep ? pmin + (long long)(kk >> 6) : pm;
+        out.pm = keep ? pref + (long long)(kk >> 6) : pm;
         out.bit = keep ? (kk & 1u) : 0u;
+        out.pref = pref + (long long)(__shfl_sync(kFull, kk, 0, LW) >> 6);
     } else {
         const unsigned long long base = ((unsigned long long)lane << 1);
         const unsigned long long k0 = valid ? (((unsigned long long)pm << 6) | base | hd) : ~0ull;
@@ -226,6 +229,7 @@ __device__ __noinline__ LeafStep list_step(int lam, long long pm, int lane, int 
         out.par = keep ? (int)((kk >> 1) & 31ull) : lane;
         out.pm = keep ? (long long)(kk >> 6) : pm;
         out.bit = keep ? (unsigned)(kk & 1ull) : 0u;
+        out.pref = (long long)(__shfl_sync(kFull, kk, 0, LW) >> 6);
     }
     return out;
 }
@@ -237,7 +241,8 @@ __device__ __forceinline__ uint64_t info_leaf(SclCtx<FZ> &cx, PathState<N> &st) 
         // one path: the child with the smaller key is always the hard decision
         return lam < 0 ? 1u : 0u;
     } else {
-        const LeafStep o = list_step<LW>(lam, st.pm, cx.lane, cx.count, cx.L);
+        const LeafStep o = list_step<LW>(lam, st.pm, cx.lane, cx.count, cx.L, cx.pref);
+        cx.pref = o.pref;
         clone_src<N, LW, I, 2>(st, o.par);
         clone_bsrc<N, LW, I, 1>(st, o.par);
         st.pm = o.pm;
@@ -352,6 +357,7 @@ __global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32) scl_kernel(const
     cx.ych = s_y[warp][seg];
     cx.lane = sl;
     cx.count = 1;
+    cx.pref = 0;
     cx.L = a.L;
     cx.fz = fz;
     PathState<N> st;
