@@ -205,7 +205,9 @@ MPWSD_API int mpwsd_decode(mpwsd_code *code, const float *y_dev, int64_t B, int 
  * the whole batch, and the results are copied back on `stream`. Everything is
  * enqueued and the call returns without waiting: the host buffers must stay
  * valid, and the results are there once `stream` has been synchronised. Uses
- * the handle's internal workspace and device staging buffers for y, cw and
+ * the handle's internal workspace and device staging buffers for y (two,
+ * used by turns: without use_graph the input copies of a call run while the
+ * stage 2 of the call before it, on the other buffer, still runs), cw and
  * flags (grown on demand with cudaMalloc; a growth waits for the device);
  * concurrent calls on one handle must be serialised by the caller. Errors as
  * in mpwsd_decode.

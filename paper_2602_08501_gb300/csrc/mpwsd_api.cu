@@ -115,8 +115,15 @@ struct mpwsd_code {
     std::vector<GraphEnt> graphs;
     cudaStream_t capture_stream = nullptr;
     // mpwsd_decode_host: device staging buffers, the stream that carries the
-    // input copies, and the events that order each chunk's stage 1 after its copy
+    // input copies, and the events that order each chunk's stage 1 after its copy.
+    // Calls alternate between two input buffers, so the copies of one call can run
+    // while the stage 2 of the call before it still reads the other buffer;
+    // stage_done[b] marks the end of the last call that used buffer b.
     float *stage_y = nullptr;
+    float *stage_y2 = nullptr;
+    int stage_next = 0;
+    cudaEvent_t stage_done[2] = {};
+    bool stage_used[2] = {};
     uint64_t *stage_cw = nullptr;
     uint16_t *stage_fl = nullptr;
     int64_t stage_B = 0;
@@ -602,7 +609,10 @@ extern "C" void mpwsd_free_code(mpwsd_code *code) {
     if (code->copy_stream) cudaStreamDestroy(code->copy_stream);
     for (auto e : code->copy_ev)
         if (e) cudaEventDestroy(e);
+    for (auto e : code->stage_done)
+        if (e) cudaEventDestroy(e);
     cudaFree(code->stage_y);
+    cudaFree(code->stage_y2);
     cudaFree(code->stage_cw);
     cudaFree(code->stage_fl);
     mpwsd_workspace_free(code->default_ws);
@@ -675,6 +685,7 @@ struct HostIO {
     const float *y = nullptr;
     uint64_t *cw = nullptr;
     uint16_t *fl = nullptr;
+    int buf = 0;  // which of the two staging input buffers y_dev is
 };
 
 static cudaError_t stage1_launch(mpwsd_code *code, Workspace &ws, const float *y_dev, int64_t f0, int64_t B, int L,
@@ -727,12 +738,18 @@ static int decode_impl(mpwsd_code *code, Workspace &ws, const float *y_dev, int6
     if (!host) {
         e = stage1_launch(code, ws, y_dev, 0, B, L, o, cw_dev, flags_dev, s);
     } else {
-        // chunk i is copied on the copy stream, then its stage 1 runs on s; the
-        // copies start after everything already on s (which may still read y_dev)
+        // chunk i is copied on the copy stream, then its stage 1 runs on s. The
+        // copies start after the last call that used this staging buffer (the call
+        // before this one used the other buffer, and its stage 2 may still run);
+        // inside a graph capture they start after everything already on s
         const int nch = (int)std::max<int64_t>(1, std::min<int64_t>(kHostChunks, B / kHostChunkFrames));
-        cudaEvent_t fork = code->copy_ev[kHostChunks];
-        e = cudaEventRecord(fork, s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(code->copy_stream, fork, 0);
+        if (t_capturing) {
+            cudaEvent_t fork = code->copy_ev[kHostChunks];
+            e = cudaEventRecord(fork, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(code->copy_stream, fork, 0);
+        } else if (code->stage_used[host->buf]) {
+            e = cudaStreamWaitEvent(code->copy_stream, code->stage_done[host->buf], 0);
+        }
         for (int i = 0; i < nch && e == cudaSuccess; ++i) {
             const int64_t a = B * i / nch, b = B * (i + 1) / nch;
             e = cudaMemcpyAsync((void *)(y_dev + a * d.n), host->y + a * d.n, (size_t)(b - a) * d.n * sizeof(float),
@@ -942,25 +959,39 @@ extern "C" int mpwsd_decode_host(mpwsd_code *code, const float *y_host, int64_t 
         if (!code->copy_stream) e = cudaStreamCreateWithFlags(&code->copy_stream, cudaStreamNonBlocking);
         for (auto &ev : code->copy_ev)
             if (e == cudaSuccess && !ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        for (auto &ev : code->stage_done)
+            if (e == cudaSuccess && !ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(e, "creating the copy stream");
         if (code->stage_B < B) {
             // a growth waits for the device (cudaFree); graphs keyed on the old buffers never match again
             cudaFree(code->stage_y);
+            cudaFree(code->stage_y2);
             cudaFree(code->stage_cw);
             cudaFree(code->stage_fl);
             code->stage_y = nullptr;
+            code->stage_y2 = nullptr;
             code->stage_cw = nullptr;
             code->stage_fl = nullptr;
             code->stage_B = 0;
+            code->stage_used[0] = code->stage_used[1] = false;  // cudaFree waited for every use
             e = dev_alloc((void **)&code->stage_y, (size_t)B * code->d.n * sizeof(float));
+            if (e == cudaSuccess) e = dev_alloc((void **)&code->stage_y2, (size_t)B * code->d.n * sizeof(float));
             if (e == cudaSuccess) e = dev_alloc((void **)&code->stage_cw, (size_t)B * code->d.W * sizeof(uint64_t));
             if (e == cudaSuccess) e = dev_alloc((void **)&code->stage_fl, (size_t)B * sizeof(uint16_t));
             if (e != cudaSuccess) return cuda_fail(e, "allocating the staging buffers");
             code->stage_B = B;
         }
+        io.buf = code->stage_next;
+        code->stage_next ^= 1;
     }
-    return run_decode(code, ws->w, code->stage_y, B, L, T, o, code->stage_cw, code->stage_fl, (cudaStream_t)stream,
-                      &io);
+    st = run_decode(code, ws->w, io.buf ? code->stage_y2 : code->stage_y, B, L, T, o, code->stage_cw, code->stage_fl,
+                    (cudaStream_t)stream, &io);
+    if (st) return st;
+    // everything this call does is on the stream now: the end of its use of the input buffer
+    cudaError_t e = cudaEventRecord(code->stage_done[io.buf], (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "recording the end of the call");
+    code->stage_used[io.buf] = true;
+    return MPWSD_OK;
 }
 
 extern "C" int mpwsd_stage1_list(mpwsd_code *code, const float *y_dev, int64_t B, int L, uint64_t *list_cw_dev,

@@ -79,3 +79,21 @@ def test_host_decode_rejects_device_tensors(mp):
     code = mp.Code.rm(6, 2, crc_poly=0x21, crc_len=6, weights=[16])
     with pytest.raises(TypeError):
         code.decode_host(torch.zeros((4, 64), device="cuda"), 8, 4)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_host_decodes_back_to_back(mp, use_graph):
+    """Calls alternate between two device input buffers: the input copies of a
+    call may run while the call before it still decodes. Four back-to-back calls
+    on different inputs, with no synchronisation between them, each equal the
+    device-buffer decode of their own input."""
+    code = mp.Code.rm(6, 2, crc_poly=0x21, crc_len=6, weights=[16])
+    B = 200_000
+    ys = [synth.make_workload("rm26_crc6", 1.0, B, seed=s).y for s in (41, 42, 43, 44)]
+    pins = [torch.from_numpy(y).pin_memory() for y in ys]
+    outs = [code.decode_host(p, 8, 4, use_graph=use_graph) for p in pins]
+    torch.cuda.synchronize()
+    for y, (cw, fl) in zip(ys, outs):
+        rcw, rfl = _device_decode(code, y, 8, 4)
+        assert np.array_equal(to_words(cw), rcw)
+        assert np.array_equal(fl.numpy(), rfl)
