@@ -102,9 +102,11 @@ struct SclCtx {
     FZ fz;
 };
 
+// sign(a) sign(b) min(|a|,|b|) with sign(0) = +1, as max(min(a,b), -max(a,b)):
+// both >= 0 gives min(a,b); both <= 0 gives -max(a,b) = min(|a|,|b|); mixed
+// signs give the larger of two non-positive values, -min(|a|,|b|)
 __device__ __forceinline__ int minsum_f(int a, int b) {
-    int m = min(abs(a), abs(b));
-    return ((a ^ b) < 0) ? -m : m;  // sign(a) sign(b) min(|a|,|b|), sign(0) = +1
+    return max(min(a, b), -max(a, b));
 }
 
 template <int N, int S>
