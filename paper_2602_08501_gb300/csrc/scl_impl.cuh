@@ -95,6 +95,7 @@ template <class FZ>
 struct SclCtx {
     const int *ych;                // channel LLRs of this frame (shared memory)
     int lane;                      // lane within the frame's segment
+    uint32_t dirs;                 // directions of this lane's sorting-network stages
     int count;                     // current list size (uniform over the warp)
     long long pref;                // lower bound on every path metric of the frame
     int L;
@@ -158,18 +159,31 @@ struct LeafStep {
     unsigned bit;   // decided u of this lane's path
 };
 
+// Which stages of the bitonic sort below keep the smaller key at this lane:
+// bit s for stage s (stages in network order). It depends only on the lane,
+// so each thread computes it once instead of at every stage of every list step.
+template <int LW>
+__device__ __forceinline__ uint32_t sort_dirs(int lane) {
+    uint32_t d = 0;
+    int s = 0;
+    for (int k = 2; k <= LW; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1, ++s)
+            if (((lane & k) == 0) == ((lane & j) == 0)) d |= 1u << s;
+    return d;
+}
+
 // Bitonic sort of one key per lane over the LW lanes of a frame (ascending in
 // lane order): each stage compares with the lane j apart and keeps the smaller
-// or the larger key by the lane's place in the network.
+// or the larger key by the lane's place in the network (dirs = sort_dirs).
 template <int LW, class K>
-__device__ __forceinline__ K seg_sort(K x, int lane) {
+__device__ __forceinline__ K seg_sort(K x, uint32_t dirs) {
+    int s = 0;
 #pragma unroll
     for (int k = 2; k <= LW; k <<= 1) {
 #pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1, ++s) {
             const K o = __shfl_xor_sync(kFull, x, j, LW);
-            const bool lo = ((lane & k) == 0) == ((lane & j) == 0);
-            x = lo ? min(x, o) : max(x, o);
+            x = (dirs & (1u << s)) ? min(x, o) : max(x, o);
         }
     }
     return x;
@@ -202,7 +216,7 @@ __device__ __forceinline__ K seg_merge_low(K a, K b, int lane) {
 // below it); when every relative metric of the segment fits 25 bits the keys
 // fit 32 bits (the usual case), otherwise the same network runs on 64-bit keys.
 template <int LW>
-__device__ __noinline__ LeafStep list_step(int lam, long long pm, int lane, int count, int L, long long pref) {
+__device__ __noinline__ LeafStep list_step(int lam, long long pm, int lane, uint32_t dirs, int count, int L, long long pref) {
     const unsigned hd = lam < 0 ? 1u : 0u;
     const long long a = lam < 0 ? -(long long)lam : (long long)lam;
     const bool valid = lane < count;
@@ -218,7 +232,7 @@ __device__ __noinline__ LeafStep list_step(int lam, long long pm, int lane, int 
         const uint32_t base32 = (uint32_t)lane << 1;
         const uint32_t q0 = valid ? (((uint32_t)d0 << 6) | base32 | hd) : 0xffffffffu;
         const uint32_t q1 = valid ? (((uint32_t)(d0 + a) << 6) | base32 | (hd ^ 1u)) : 0xffffffffu;
-        const uint32_t kk = seg_merge_low<LW>(seg_sort<LW>(q0, lane), seg_sort<LW>(q1, lane), lane);
+        const uint32_t kk = seg_merge_low<LW>(seg_sort<LW>(q0, dirs), seg_sort<LW>(q1, dirs), lane);
         out.par = keep ? (int)((kk >> 1) & 31u) : lane;
         out.pm = keep ? pref + (long long)(kk >> 6) : pm;
         out.bit = keep ? (kk & 1u) : 0u;
@@ -227,7 +241,7 @@ __device__ __noinline__ LeafStep list_step(int lam, long long pm, int lane, int 
         const unsigned long long base = ((unsigned long long)lane << 1);
         const unsigned long long k0 = valid ? (((unsigned long long)pm << 6) | base | hd) : ~0ull;
         const unsigned long long k1 = valid ? (((unsigned long long)(pm + a) << 6) | base | (hd ^ 1u)) : ~0ull;
-        const unsigned long long kk = seg_merge_low<LW>(seg_sort<LW>(k0, lane), seg_sort<LW>(k1, lane), lane);
+        const unsigned long long kk = seg_merge_low<LW>(seg_sort<LW>(k0, dirs), seg_sort<LW>(k1, dirs), lane);
         out.par = keep ? (int)((kk >> 1) & 31ull) : lane;
         out.pm = keep ? (long long)(kk >> 6) : pm;
         out.bit = keep ? (unsigned)(kk & 1ull) : 0u;
@@ -243,7 +257,7 @@ __device__ __forceinline__ uint64_t info_leaf(SclCtx<FZ> &cx, PathState<N> &st) 
         // one path: the child with the smaller key is always the hard decision
         return lam < 0 ? 1u : 0u;
     } else {
-        const LeafStep o = list_step<LW>(lam, st.pm, cx.lane, cx.count, cx.L, cx.pref);
+        const LeafStep o = list_step<LW>(lam, st.pm, cx.lane, cx.dirs, cx.count, cx.L, cx.pref);
         cx.pref = o.pref;
         clone_src<N, LW, I, 2>(st, o.par);
         clone_bsrc<N, LW, I, 1>(st, o.par);
@@ -277,12 +291,9 @@ __device__ __forceinline__ uint64_t node(SclCtx<FZ> &cx, PathState<N> &st) {
         // min-sum updates satisfy P(f(a, b)) + P(a + b) = P(a) + P(b), so the
         // leaves' metric increments add up to sum_k P(input_k) of this node
         // (integers: exactly the leaf-by-leaf sum), and its codeword is 0
-        long long add = 0;
+        int add = 0;  // at most 2^23 N <= 2^30: every input of a node of size S is at most 2^23 N / S
 #pragma unroll
-        for (int k = 0; k < S; ++k) {
-            const int x = st.llr[S + k];
-            add += x < 0 ? -(long long)x : 0ll;
-        }
+        for (int k = 0; k < S; ++k) add += max(-st.llr[S + k], 0);
         st.pm += add;
         return 0;
     } else {
@@ -358,6 +369,7 @@ __global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32) scl_kernel(const
     SclCtx<FZ> cx;
     cx.ych = s_y[warp][seg];
     cx.lane = sl;
+    cx.dirs = sort_dirs<LW>(sl);
     cx.count = 1;
     cx.pref = 0;
     cx.L = a.L;
