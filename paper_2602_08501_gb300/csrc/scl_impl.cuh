@@ -447,9 +447,12 @@ __global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32) scl_kernel(const
     }
     slot = __shfl_sync(segmask, slot, 0, LW);
     base = __shfl_sync(segmask, base, 0, LW);
+    // ||y||_1 on the grid, summed across the segment's lanes (exact: < 2^30)
+    int l1 = 0;
+    for (int j = sl; j < N; j += LW) l1 += abs(cx.ych[j]);
+#pragma unroll
+    for (int o = LW / 2; o >= 1; o >>= 1) l1 += __shfl_xor_sync(segmask, l1, o, LW);
     if (sl == 0) {
-        int l1 = 0;
-        for (int j = 0; j < N; ++j) l1 += abs(cx.ych[j]);
         // a pool slot keeps its own copy of y, so y is read at the slot itself
         a.ws.slot_frame[slot] = pool ? slot : (int)(a.f0 + frame);
         a.ws.slot_l1[slot] = (float)l1 * (1.0f / 524288.0f);
