@@ -275,7 +275,7 @@ __device__ __forceinline__ uint64_t leaf(SclCtx<FZ> &cx, PathState<N> &st) {
         frz = cx.fz.template frozen<I>();
     if (frz) {
         const int lam = st.llr[1];
-        if (lam < 0) st.pm -= lam;  // decided bit 0 disagrees with HD = 1
+        st.pm += max(-lam, 0);  // decided bit 0 disagrees with HD = 1 when lam < 0
         return 0;
     }
     return info_leaf<N, LW, FZ, I>(cx, st);
