@@ -330,8 +330,8 @@ MPWSD_API int mpwsd_pool_step(mpwsd_pool *pool, void *stream);
  *    score without it and can run slower than through mpwsd_decode; the
  *    results are identical.
  *  - Set-up: the first call on each device (with that device current) looks
- *    up the array's device address; make that first call before any stream
- *    capture begins.
+ *    up the array's device address (cudaGetSymbolAddress, not an allocation)
+ *    and keeps it for later calls.
  *  - Sharing: every call on a device uses the same array and finds the
  *    previous call's contents in it (the counters it needs zeroed are cleared
  *    on the stream). Calls whose work overlaps on the GPU, on any stream or
