@@ -346,10 +346,14 @@ struct SclShape {
     static constexpr int kBytesPerWarp = kFPW * N * 4;
     static constexpr int kWarps = kBytesPerWarp * kWarpsPerBlock <= 32768 ? kWarpsPerBlock
                                   : (kBytesPerWarp * 2 <= 32768 ? 2 : 1);
+    // n = 64 with 2 to 16 lanes per frame: 7 blocks of 4 warps per SM (at most 72
+    // registers a thread, 28 warps instead of the 24 that 80 registers allow)
+    static constexpr bool kOcc = N == 64 && LW > 1 && LW < 32 && kWarps == 4;
+    static constexpr int kMinBlocks = 7;
 };
 
 template <int N, int LW, class FZ>
-__global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32) scl_kernel(const SclArgs a, const CodeDev c, const FZ fz) {
+__device__ __forceinline__ void scl_body(const SclArgs &a, const CodeDev &c, const FZ &fz) {
     constexpr int FPW = SclShape<N, LW>::kFPW;
     constexpr int WPB = SclShape<N, LW>::kWarps;
     constexpr int W = (N + 63) / 64;
@@ -509,12 +513,27 @@ __global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32) scl_kernel(const
 }
 
 template <int N, int LW, class FZ>
+__global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32) scl_kernel(const SclArgs a, const CodeDev c, const FZ fz) {
+    scl_body<N, LW, FZ>(a, c, fz);
+}
+
+// the same kernel with the register bound of SclShape::kMinBlocks resident blocks
+template <int N, int LW, class FZ>
+__global__ void __launch_bounds__(SclShape<N, LW>::kWarps * 32, SclShape<N, LW>::kMinBlocks)
+    scl_kernel_occ(const SclArgs a, const CodeDev c, const FZ fz) {
+    scl_body<N, LW, FZ>(a, c, fz);
+}
+
+template <int N, int LW, class FZ>
 cudaError_t launch_one(const CodeDev &c, const SclArgs &a, const FZ &fz, cudaStream_t s) {
     constexpr int WPB = SclShape<N, LW>::kWarps;
     constexpr int FPB = WPB * (32 / LW);
     const int64_t blocks = (a.B + FPB - 1) / FPB;
     if (blocks == 0) return cudaSuccess;
-    scl_kernel<N, LW, FZ><<<(unsigned)blocks, WPB * 32, 0, s>>>(a, c, fz);
+    if constexpr (SclShape<N, LW>::kOcc)
+        scl_kernel_occ<N, LW, FZ><<<(unsigned)blocks, WPB * 32, 0, s>>>(a, c, fz);
+    else
+        scl_kernel<N, LW, FZ><<<(unsigned)blocks, WPB * 32, 0, s>>>(a, c, fz);
     return cudaGetLastError();
 }
 
