@@ -35,7 +35,7 @@ def _dev(a, dtype=torch.float32):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
 
 
-@pytest.mark.parametrize("L", [1, 2, 5, 8, 32])
+@pytest.mark.parametrize("L", [1, 2, 3, 5, 8, 16, 32])
 def test_stage1_list_bit_exact_rm26(mp, rm26, rm26_or, oracle_mod, L):
     wl = synth.make_workload("rm26_crc6", 1.0, 301, seed=7)
     cw, pm = rm26.stage1_list(_dev(wl.y), L)
